@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Fock builds/s of the density-fitted RHF Fock build at (H2O)_64 on GB300.
+
+One step = one Fock build F = H + 2J - K from C_occ (bqc_jk): the X pass
+(X_P = B_P C_occ with the fused Coulomb contraction w_P), the J pass and the
+K contraction, with B (N = 1600, Naux = 4800, nocc = 320) resident in HBM.
+The headline runs in mixed precision (TF32 tcgen05 tensor cores, FP32
+accumulation, FP64 chunk sums); the plain-FP64 build is timed beside it.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun, each rank runs an independent replica (weak scaling, no
+collective on the data path).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Fock builds/s at (H2O)_64, mixed vs FP64 at <=1e-6 Eh; serve p50/p99 ms"
+UNIT = "Fock builds/s"
+# TF32 dense peak = measured bf16 x nominal (1.1 / 2.25) ratio of the recipe
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--waters", type=int, default=64)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() in ("active", "0x1", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and all(v.strip().isdigit() for v in ids) and local_rank < len(ids):
+        return int(ids[local_rank])
+    return local_rank
+
+
+def cpu_baseline(mol, nsample: int, reps: int = 1):
+    """Oracle Fock build (numpy/BLAS FP64, oracle.jk_df as it stands) on a
+    sample of nsample auxiliary functions with seeded data of the workload's
+    shape; extrapolated linearly in Naux (the build is a sum over P)."""
+    import numpy as np
+
+    import oracle
+    n = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.orb)
+    naux = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.aux)
+    rng = np.random.default_rng(2025)
+    B = rng.standard_normal((nsample, n, n))
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    C = rng.standard_normal((n, mol.nocc)) * 0.05
+    oracle.jk_df(B[:2], C)  # warm the BLAS
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.jk_df(B, C)
+    dt = (time.perf_counter() - t0) / reps
+    per_build = dt * naux / nsample
+    return {"value": 1.0 / per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle.jk_df on {nsample} of {naux} aux functions (N={n}, nocc={mol.nocc}), "
+                      f"seeded data, {reps} rep(s), {dt:.2f} s; extrapolated x{naux / nsample:.0f}"}
+
+
+def run_reference(args, rank, world):
+    import workload
+    mol = workload.water_cluster(args.waters)
+    if rank != 0:
+        return
+    nsample = 64
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(mol, nsample)
+        if i >= args.warmup:
+            times.append(1.0 / r["value"])
+    per = statistics.mean(times)
+    v = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(mol, "oracle"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(mol, prec):
+    n = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.orb)
+    naux = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.aux)
+    return {"workload": f"{mol.name} DF-RHF Fock build, stored B, N={n}, Naux={naux}, "
+                        f"nocc={mol.nocc}", "prec": prec, "seed": len(mol.Z) // 3,
+            "l2": "inputs larger than L2 (TF32 B shadow 49 GB streamed per step)",
+            "parallelism": "replicas"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_2502_17963_gb300 as bqc
+    import workload
+    from paper_2502_17963_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    mol = workload.water_cluster(args.waters)
+    ctx = bqc.Context(local)
+    basis = bqc.Basis(ctx, mol)
+    n, no = basis.nbf, basis.nocc
+    t0 = time.perf_counter()
+    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED, keep_fp32=True)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    # occupied orbitals of a physical state: two mixed SCF iterations from the core guess
+    r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32, max_iter=2, keep_arrays=True)
+    C = r["C"][:, :no].contiguous()
+    J = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    K = torch.empty_like(J)
+    stream = torch.cuda.current_stream()
+    MIX = bqc.PREC_MIXED_TF32
+    for _ in range(max(3, args.warmup)):
+        df.jk(C, MIX, J, K)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    df.timing(True)
+    phases = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        df.jk(C, MIX, J, K)
+        phases.append(df.phase_ms())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    df.timing(False)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms * 1e-3)
+    ph = np.array(phases)
+    ph_mean = ph.mean(axis=0).tolist()
+
+    # plain FP64 build at the same C_occ, and the Fock-matrix difference
+    J64 = torch.empty_like(J)
+    K64 = torch.empty_like(J)
+    fp64 = None
+    if args.fp64_steps > 0:
+        df.jk(C, bqc.PREC_FP64, J64, K64)  # warm
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            df.jk(C, bqc.PREC_FP64, J64, K64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        df.jk(C, MIX, J, K)
+        dF = (2.0 * (J - J64) - (K - K64)).abs().max().item()
+        fp64 = {"builds_per_s": 1e3 / fms, "ms_per_build": fms, "steps": args.fp64_steps,
+                "max_abs_dF_mixed_vs_fp64": dF,
+                "speedup_mixed_over_fp64": fms / ms_per_step}
+
+    # end to end through the C ABI with host buffers (H2D of C_occ, D2H of J, K)
+    e2e = None
+    if not args.no_e2e:
+        Ch = torch.empty((n, no), dtype=torch.float64, pin_memory=True)
+        Ch.copy_(C.cpu())
+        Jh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        Kh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        Cn, Jn, Kn = Ch.numpy(), Jh.numpy(), Kh.numpy()
+        for _ in range(2):
+            df.jk_host(Cn, MIX, Jn, Kn)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            df.jk_host(Cn, MIX, Jn, Kn)
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": n * no * 8, "d2h_bytes_per_step": 2 * n * n * 8}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    pk, pk_src = peaks()
+    naux = basis.naux
+    xflops = 2.0 * naux * n * n * no   # algorithmic flops of one X pass
+    xs = ph_mean[0] * 1e-3
+    tf32_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")) * TF32_OVER_BF16
+    achieved = xflops / xs / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_xpass_tf32 (X = B C, fused w)",
+                "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None,
+                "peak_source": f"{pk_src}: bf16 sustained x nominal tf32/bf16 (1.1/2.25)",
+                "algorithmic_per_launch": f"2*Naux*N^2*nocc = {xflops:.4g} flop"}
+    jbytes = naux * n * (n + 1) / 2 * 4  # one read of the TF32 lower triangle
+    kflops = n * n * naux * no           # SYRK half
+    extra = {
+        "phases_ms": {"x_pass": ph_mean[0], "j_pass": ph_mean[1], "k_syrk": ph_mean[2],
+                      "prep": ph_mean[3]},
+        "j_pass_gbs": jbytes / (ph_mean[1] * 1e-3) / 1e9,
+        "j_pass_frac_hbm": jbytes / (ph_mean[1] * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "k_syrk_tflops": kflops * 2 / (ph_mean[2] * 1e-3) / 1e12,
+        "setup_s": setup_s,
+        "fp64": fp64,
+    }
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+            "config": config(mol, "mixed_tf32"), "roofline": roofline,
+            "gpu_launches": 7 * args.steps, "clocks": clk, "e2e": e2e}
+    line.update(extra)
+    if not args.no_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(mol, 192)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * bqc.h - C ABI of the GB300 density-fitted RHF Fock-build library.
+ *
+ * The method is the mean-field stage of arXiv 2502.17963 (ByteQC), Sec. 2.2:
+ * three-index "Cholesky-decomposition ERIs" built from an auxiliary basis,
+ * stored once when they fit ("ERIs are only affected by the basis set and the
+ * atomic structure"), regenerated on the fly in auxiliary slices when they do
+ * not, and contracted into the Coulomb and exchange matrices inside the SCF.
+ * The paper prints no equations for this path; the operations below are the
+ * textbook ones (Szabo & Ostlund Ch. 3; Helgaker, Jorgensen & Olsen Ch. 9).
+ *
+ * Notation.  N orbital and Naux auxiliary Cartesian Gaussian functions,
+ * nocc doubly occupied orbitals, Npair = N(N+1)/2.  D = C_occ C_occ^T (no
+ * factor 2).  V_PQ = (P|Q) = L L^T (L lower, positive diagonal).
+ * B_P,mu nu = sum_Q (L^{-1})_PQ (Q|mu nu).  J = sum_P B_P (B_P : D),
+ * K = sum_P B_P D B_P, F = H + 2J - K, E = sum D (H + F) + E_nn.
+ *
+ * Conventions for every call.
+ *  - Return value: BQC_OK (0) or a negative status; bqc_strerror() names it.
+ *    No call aborts, throws or traps; a device-side check that trips is
+ *    reported as BQC_E_DEVICE_FLAG by the next call that reads the flag.
+ *  - Pointers named *_dev are device pointers on the context's device; all
+ *    other pointers are host memory.  Matrices are row-major, FP64 unless a
+ *    name says otherwise.
+ *  - Ownership: the caller owns every array it passes; the library copies
+ *    what it keeps.  Handles are owned by the library until their _destroy.
+ *  - Streams: a cudaStream_t argument may be NULL (the legacy default
+ *    stream).  Calls marked "async" enqueue work and return without waiting.
+ *  - Units: bohr and hartree.  Cartesian components of a shell of angular
+ *    momentum l are ordered lexicographically (xx, xy, xz, yy, yz, zz ...);
+ *    every Cartesian primitive component is unit-normalised and each
+ *    contracted shell is rescaled to unit self-overlap.
+ */
+#ifndef BQC_H
+#define BQC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *bqc_stream_t; /* = cudaStream_t */
+
+enum {
+  BQC_OK = 0,
+  BQC_E_INVALID = -1,       /* bad argument or size                         */
+  BQC_E_OOM = -2,           /* allocation failed                            */
+  BQC_E_ADMISSION = -3,     /* request exceeds the HBM budget               */
+  BQC_E_NOT_CONVERGED = -4, /* SCF hit max_iter                             */
+  BQC_E_CUDA = -5,          /* a CUDA runtime / library call failed         */
+  BQC_E_TIMEOUT = -6,       /* a bounded device or host wait ran out        */
+  BQC_E_DEVICE_FLAG = -7,   /* a kernel's own bounds check tripped          */
+  BQC_E_NOT_READY = -8,     /* serving: result not available yet            */
+  BQC_E_UNSUPPORTED = -9    /* angular momentum / size beyond this build    */
+};
+
+/* Precision of the Fock build (the K contraction and B.D products).
+ * FP64: all FP64 (DFMA).  MIXED_TF32: B and C_occ shadows rounded to TF32,
+ * tcgen05 kind::tf32 MMAs with FP32 accumulation, chunk sums in FP64. */
+typedef enum { BQC_PREC_FP64 = 0, BQC_PREC_MIXED_TF32 = 1 } bqc_prec;
+
+typedef struct bqc_ctx bqc_ctx;
+typedef struct bqc_basis bqc_basis;
+typedef struct bqc_df bqc_df;
+typedef struct bqc_server bqc_server;
+
+/* Device-memory callbacks.  alloc returns a device pointer (or NULL) of at
+ * least `bytes` bytes on the context's device; free releases it.  Both may be
+ * NULL, in which case cudaMalloc / cudaFree are used. */
+typedef void *(*bqc_alloc_fn)(size_t bytes, void *user);
+typedef void (*bqc_free_fn)(void *ptr, void *user);
+
+/* Create a context on `device`.  hbm_budget (bytes) caps what the serving
+ * loop admits (0 = no cap).  Builds the Boys-function table on the device. */
+int bqc_ctx_create(int device, size_t hbm_budget, bqc_alloc_fn alloc, bqc_free_fn dealloc,
+                   void *alloc_user, bqc_ctx **out);
+int bqc_ctx_destroy(bqc_ctx *ctx);
+
+/* One contracted Cartesian shell.  exps/coefs: nprim entries each; coefs
+ * multiply unit-normalised primitives. */
+typedef struct {
+  int atom;
+  int l;
+  int nprim;
+  const double *exps;
+  const double *coefs;
+} bqc_shell;
+
+/* Load a molecule and its orbital and auxiliary bases (Sec. 2.2: DF needs
+ * an "auxiliary artificial molecule").  Z: natom nuclear charges; xyz_bohr:
+ * natom x 3.  Orbital l <= 2 and auxiliary l <= 3 in this build (up to the
+ * (f|dd) class), else BQC_E_UNSUPPORTED; sum Z must be even (closed shell),
+ * else BQC_E_INVALID.  Copies everything; the shell setup (normalisation,
+ * pair classes) runs here. */
+int bqc_basis_load(bqc_ctx *ctx, int natom, const int *Z, const double *xyz_bohr,
+                   const bqc_shell *orb, int norb_shell, const bqc_shell *aux, int naux_shell,
+                   bqc_basis **out);
+int bqc_basis_destroy(bqc_basis *basis);
+/* Sizes: N, Naux, nocc, number of orbital shell pairs (a >= b). */
+int bqc_basis_info(const bqc_basis *basis, int *nbf, int *naux, int *nocc, int64_t *nshell_pair);
+/* Nuclear repulsion energy sum_{A<B} Z_A Z_B / R_AB. */
+int bqc_basis_enuc(const bqc_basis *basis, double *enuc);
+
+/* One-electron matrices (overlap S, kinetic T, nuclear attraction Vne),
+ * N x N into device buffers; any pointer may be NULL to skip it.  Async. */
+int bqc_one_electron(const bqc_basis *basis, double *S_dev, double *T_dev, double *Vne_dev,
+                     bqc_stream_t stream);
+
+/* Boys function F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt, m = 0..mmax (<= 16)
+ * for n arguments: out_dev is n x (mmax+1).  The device evaluator used by the
+ * integral kernels (Taylor table + recursions), exposed for testing.  Async. */
+int bqc_boys(bqc_ctx *ctx, int n, const double *T_dev, int mmax, double *out_dev,
+             bqc_stream_t stream);
+
+/* Coulomb metric V_PQ = (P|Q), Naux x Naux, FP64.  Async. */
+int bqc_int2c(const bqc_basis *basis, double *V_dev, bqc_stream_t stream);
+
+/* Raw three-centre integrals (P|mu nu) over all aux functions and the packed
+ * lower triangle mu >= nu: out_dev is Naux x Npair, column mu(mu+1)/2 + nu.
+ * Integrals whose Schwarz bound sqrt((P|P)) sqrt((mu nu|mu nu)) is below
+ * `schwarz` are written as 0 (schwarz <= 0 computes everything).  Async. */
+int bqc_int3c(const bqc_basis *basis, double schwarz, double *out_dev, bqc_stream_t stream);
+
+/* ---------------------------------------------------------- DF tensor --- */
+
+typedef enum { BQC_DF_STORED = 0, BQC_DF_DIRECT = 1, BQC_DF_AUTO = 2 } bqc_df_mode;
+
+typedef struct {
+  int mode;            /* bqc_df_mode                                         */
+  double schwarz;      /* screening threshold; default 1e-12 stored, 1e-10 direct */
+  int aux_block;       /* direct mode: aux functions per block (default 1024)  */
+  int keep_fp32;       /* stored mode: also keep the TF32-rounded full-square shadow */
+  size_t hbm_limit;    /* AUTO: choose DIRECT when STORED needs more (0 = free memory) */
+} bqc_df_opts;
+
+/* Build the DF machinery (Sec. 2.2).  STORED: metric, Cholesky, raw (Q|mu nu),
+ * in-place B = L^{-1}(Q|mu nu) in FP64 (packed), plus the TF32 full-square
+ * shadow when keep_fp32.  DIRECT: metric, Cholesky and screening data only;
+ * (Q|mu nu) is regenerated in aux blocks at each bqc_jk ("on-the-fly",
+ * "slice-by-slice", Sec. 2.2).  Work on `stream`; returns after the build has
+ * been enqueued and its workspaces allocated (synchronises the stream once to
+ * size the screened work lists).  opts may be NULL for defaults. */
+int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
+                 bqc_stream_t stream, bqc_df **out);
+int bqc_df_destroy(bqc_df *df);
+/* Mode actually built and bytes of device memory held. */
+int bqc_df_info(const bqc_df *df, int *mode, size_t *device_bytes);
+/* Copy B (Naux x Npair packed, FP64, stored mode) into a device buffer; or
+ * the Cholesky factor L (Naux x Naux, lower, zeros above) when which = 1.  Async. */
+int bqc_df_copy(const bqc_df *df, int which, double *out_dev, bqc_stream_t stream);
+
+/* J and K for the occupied orbitals C_occ (N x nocc, row-major, device):
+ * J_mu nu = sum_P B_P,mu nu w_P with w_P = sum_lambda sigma B_P,lambda sigma D_lambda sigma,
+ * K_mu nu = sum_{P,i} X_P,mu i X_P,nu i with X_P = B_P C_occ (Sec. 2.2: the
+ * Coulomb matrix needs two passes over the CD-ERIs; exchange re-reads them).
+ * J_dev, K_dev: N x N, FP64, full symmetric.  nocc must equal the basis'
+ * nocc.  Async; no host synchronisation and no allocation inside, so the
+ * call can be captured into a CUDA graph (stored mode). */
+int bqc_jk(bqc_df *df, const double *C_occ_dev, int nocc, int prec, double *J_dev,
+           double *K_dev, bqc_stream_t stream);
+
+/* Same as bqc_jk with host buffers: copies C_occ in, J and K out, and
+ * waits for the stream.  The end-to-end entry point. */
+int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, double *K,
+                bqc_stream_t stream);
+
+/* Per-phase device timing of bqc_jk (a profiling aid).  enable != 0 makes
+ * every following bqc_jk on this handle record CUDA events at its phase
+ * boundaries on its stream (leave it off while capturing a graph).
+ * bqc_df_phase_ms waits for the last call's events and writes up to n
+ * durations in ms: [0] X pass (X = B C with the fused w contraction),
+ * [1] J pass, [2] K (SYRK and its FP64 reduction), [3] operand preparation
+ * and unpacking.  BQC_E_NOT_READY if no timed call has been made. */
+int bqc_df_timing(bqc_df *df, int enable);
+int bqc_df_phase_ms(bqc_df *df, float *ms, int n);
+
+/* ---------------------------------------------------------------- SCF --- */
+
+typedef struct {
+  double diis_tol;     /* max |X^T (FDS - SDF) X| to converge (default 1e-8)   */
+  double energy_tol;   /* |E - E_prev| to converge (default 1e-10)             */
+  double stage_tol;    /* mixed -> FP64 switch when DIIS error below (1e-5)   */
+  int max_iter;        /* default 100                                         */
+  int diis_space;      /* default 8                                           */
+  int prec;            /* bqc_prec of the first stage; FP64 = unstaged        */
+  double orth_thresh;  /* canonical orthogonalisation cut on S eigenvalues (1e-8) */
+} bqc_scf_opts;
+
+typedef struct {
+  double energy;       /* total energy at convergence (last iteration)        */
+  double e_nuc;
+  double diis_err;     /* max-abs DIIS error of the last iteration            */
+  int iterations;
+  int converged;
+  int iterations_mixed;/* iterations run in the mixed stage                    */
+  int nmo;             /* orbitals kept by canonical orthogonalisation          */
+  /* Optional caller-owned device outputs (set before the call, NULL = skip):
+   * C_dev N x N buffer receiving C as N x nmo row-major (first N*nmo
+   * entries); eps_dev N doubles (first nmo used); F_dev N x N last Fock
+   * matrix. */
+  double *C_dev;
+  double *eps_dev;
+  double *F_dev;
+} bqc_scf_result;
+
+/* Closed-shell SCF (canonical orthogonalisation, core-Hamiltonian guess,
+ * Pulay DIIS on e = X^T (FDS - SDF) X, aufbau) with the Fock build of
+ * bqc_jk.  With prec = MIXED_TF32 the first stage runs mixed and switches to
+ * FP64 (DIIS subspace cleared) when the DIIS error drops below stage_tol.
+ * Blocks until done.  Returns BQC_E_NOT_CONVERGED (result still filled) if
+ * max_iter is reached.  out's C_dev / eps_dev / F_dev are read as inputs
+ * (caller buffers or NULL); everything else in *out is written. */
+int bqc_scf_run(bqc_ctx *ctx, bqc_df *df, const bqc_scf_opts *opts, bqc_stream_t stream,
+                bqc_scf_result *out);
+
+/* ------------------------------------------------------------ serving --- */
+
+typedef struct {
+  int max_slots;       /* concurrent SCF solves on the device (default 4)     */
+  size_t hbm_budget;   /* bytes the admitted requests may hold (0 = ctx's)    */
+  int prec;            /* bqc_prec of every request                           */
+  bqc_scf_opts scf;    /* SCF options for every request                       */
+} bqc_serve_opts;
+
+typedef struct {
+  int natom;
+  const int *Z;
+  const double *xyz_bohr;
+  const bqc_shell *orb;
+  int norb_shell;
+  const bqc_shell *aux;
+  int naux_shell;
+} bqc_request;
+
+typedef struct {
+  int status;          /* BQC_OK, BQC_E_NOT_CONVERGED, BQC_E_ADMISSION, ...   */
+  double energy;
+  double diis_err;
+  int iterations;
+  int nbf;
+  double t_submit;     /* seconds on the server's monotonic clock              */
+  double t_admit;
+  double t_done;
+} bqc_serve_result;
+
+/* Continuous-batching server: a scheduler thread admits queued requests as
+ * slots and HBM budget free up; each admitted request runs its DF build and
+ * SCF on its own stream, so solves overlap on the device. */
+int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out);
+/* Copies the request; returns a ticket.  BQC_E_ADMISSION if the request could
+ * never fit the budget. */
+int bqc_serve_submit(bqc_server *srv, const bqc_request *req, uint64_t *ticket);
+/* BQC_OK with the result once done, BQC_E_NOT_READY before. */
+int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res);
+/* Wait (at most timeout_s seconds, <= 0 = no limit) until all submitted
+ * requests are done; BQC_E_TIMEOUT otherwise. */
+int bqc_serve_drain(bqc_server *srv, double timeout_s);
+int bqc_serve_destroy(bqc_server *srv);
+/* Predicted device bytes of a request of this size (the admission ledger). */
+size_t bqc_serve_footprint(int nbf, int naux, int nocc);
+
+const char *bqc_strerror(int status);
+/* Text of the last error recorded on the calling thread (file:line of the failing call). */
+const char *bqc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BQC_H */

@@ -1,0 +1,356 @@
+// Density-fitting tensor and the J/K build (Sec. 2.2).
+//
+// Stored mode ("ERIs ... only need to be calculated once and stored"):
+//   V = (P|Q) -> L (Cholesky) -> raw (Q|mu nu) packed lower triangle in FP64
+//   -> B = L^{-1} raw in place -> optional TF32-rounded full-square shadow.
+// Each Fock build then makes two passes over B, as the paper notes for the
+// Coulomb matrix: the X pass (X_P = B_P C_occ, with w_P = <X_P, C_occ>) and
+// the J pass (J = sum_P w_P B_P); K = sum_P X_P X_P^T.
+// Direct mode (on-the-fly, slice-by-slice): see direct.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "bqc_internal.h"
+#include "df_internal.h"
+#include "gemm64.cuh"
+
+namespace bqc {
+
+// w[P] = sum_{mu,i} X[P][mu][i] C[mu][i]  (one block per P, FP64).
+__global__ void __launch_bounds__(256) k_wdot(const double *X, const double *C, int64_t nc,
+                                              double *w) {
+  const int P = blockIdx.x;
+  const double *x = X + (int64_t)P * nc;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) s = fma(x[i], C[i], s);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w[P] = red[0];
+}
+
+// J pass over packed FP64 B: Jp[col] = sum_P w_P B[P][col]; each thread owns
+// two adjacent columns and streams all P (one read of B, coalesced).
+__global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
+                                                 const double *__restrict__ w, int naux,
+                                                 int64_t npair, double *__restrict__ Jp) {
+  const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (c2 >= npair) return;
+  double a0 = 0.0, a1 = 0.0;
+  if (c2 + 1 < npair && (npair % 2 == 0)) {
+    for (int P = 0; P < naux; ++P) {
+      const double2 b = __ldg(reinterpret_cast<const double2 *>(B + (int64_t)P * npair + c2));
+      const double wp = __ldg(w + P);
+      a0 = fma(wp, b.x, a0);
+      a1 = fma(wp, b.y, a1);
+    }
+    Jp[c2] = a0;
+    Jp[c2 + 1] = a1;
+  } else {
+    for (int P = 0; P < naux; ++P) {
+      const double wp = __ldg(w + P);
+      a0 = fma(wp, B[(int64_t)P * npair + c2], a0);
+      if (c2 + 1 < npair) a1 = fma(wp, B[(int64_t)P * npair + c2 + 1], a1);
+    }
+    Jp[c2] = a0;
+    if (c2 + 1 < npair) Jp[c2 + 1] = a1;
+  }
+}
+
+// Packed lower triangle -> full symmetric N x N.
+__global__ void k_unpack_sym(const double *Jp, int n, double *J) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  const int64_t r = i / n, c = i % n;
+  const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
+  J[i] = Jp[hi * (hi + 1) / 2 + lo];
+}
+
+__device__ __forceinline__ float round_tf32(double x) {
+  // round to nearest TF32 (10 explicit mantissa bits), ties away from zero
+  uint32_t r;
+  const float f = (float)x;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return __uint_as_float(r);
+}
+
+// B32[P][mu][nu] = tf32(B64[P][tri(mu, nu)]) for the full square; rows
+// padded with zeros to ld columns (TMA strides must be multiples of 16 B).
+__global__ void k_expand_tf32(const double *__restrict__ B, int n, int ld, int64_t npair, int p0,
+                              int np, float *__restrict__ B32) {
+  const int64_t nn = (int64_t)n * ld;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn * np) return;
+  const int64_t P = i / nn, rc = i % nn;
+  const int64_t r = rc / ld, c = rc % ld;
+  if (c >= n) {
+    B32[i] = 0.0f;
+    return;
+  }
+  const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
+  B32[i] = round_tf32(B[(p0 + P) * npair + hi * (hi + 1) / 2 + lo]);
+}
+
+int df_expand_tf32(const double *B64, int n, int64_t npair, int p0, int np, float *B32,
+                   cudaStream_t s) {
+  const int ld = mixed_ld(n);
+  const int64_t tot = (int64_t)n * ld * np;
+  if (!tot) return BQC_OK;
+  k_expand_tf32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B64, n, ld, npair, p0, np, B32);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {
+  const Basis *b = df->basis;
+  const int n = b->nbf, naux = b->naux, no = b->nocc;
+  const int64_t npair = df->npair;
+  double *X = df->X64.as<double>();
+  df->mark(0, s);
+  df->mark(1, s);
+  // X_P = Bsym_P C  (batched over P)
+  Gemm64Args g;
+  g.M = n;
+  g.N = no;
+  g.K1 = 1;
+  g.K2 = n;
+  g.A = df->B64.as<double>();
+  g.bsA = npair;
+  g.B = C;
+  g.ldb = no;
+  g.C = X;
+  g.ldc = no;
+  g.bsC = (int64_t)n * no;
+  g.batch = naux;
+  BQC_TRY(launch_gemm64(kASym, false, g, s));
+  k_wdot<<<naux, 256, 0, s>>>(X, C, (int64_t)n * no, df->w.as<double>());
+  BQC_LAUNCH_CHECK();
+  df->mark(2, s);
+  // J pass
+  k_jpass64<<<(unsigned)((npair / 2 + 256) / 256), 256, 0, s>>>(
+      df->B64.as<double>(), df->w.as<double>(), naux, npair, df->Jp.as<double>());
+  BQC_LAUNCH_CHECK();
+  k_unpack_sym<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(), n,
+                                                                         J);
+  BQC_LAUNCH_CHECK();
+  df->mark(3, s);
+  // K = sum_{P,i} X_P,mu i X_P,nu i
+  Gemm64Args k;
+  k.M = n;
+  k.N = n;
+  k.K1 = naux;
+  k.K2 = no;
+  k.A = X;
+  k.lda = no;
+  k.sA1 = (int64_t)n * no;
+  k.B = X;
+  k.ldb = no;
+  k.sB1 = (int64_t)n * no;
+  k.C = K;
+  k.ldc = n;
+  k.lower_only = 1;
+  k.mirror = 1;
+  BQC_TRY(launch_gemm64(kAN, true, k, s));
+  df->mark(4, s);
+  return BQC_OK;
+}
+
+size_t df_stored_bytes(int n, int naux, int nocc, bool fp32) {
+  const size_t npair = (size_t)n * (n + 1) / 2;
+  size_t b = (size_t)naux * naux * 8 + (size_t)naux * npair * 8;  // L, B64
+  b += (size_t)naux * n * nocc * 8;                                // X64
+  b += npair * 8 + (size_t)naux * 8 * 2;
+  if (fp32) {
+    b += (size_t)naux * n * mixed_ld(n) * 4;  // B32
+    b += (size_t)naux * n * nocc * 4;       // X32
+    b += (size_t)n * nocc * 4 * 2;          // C shadows
+    b += mixed_workspace_bytes(n, naux, nocc);
+  }
+  return b;
+}
+
+}  // namespace bqc
+
+using namespace bqc;
+
+extern "C" {
+
+int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
+                 bqc_stream_t stream, bqc_df **out) {
+  if (!ctx || !basis || !out) return BQC_E_INVALID;
+  *out = nullptr;
+  BQC_CUDA_TRY(cudaSetDevice(ctx->device));
+  bqc_df_opts o;
+  o.mode = BQC_DF_STORED;
+  o.schwarz = -1.0;
+  o.aux_block = 1024;
+  o.keep_fp32 = 1;
+  o.hbm_limit = 0;
+  if (opts) o = *opts;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = basis->nbf, naux = basis->naux, no = basis->nocc;
+  const int64_t npair = (int64_t)n * (n + 1) / 2;
+  int mode = o.mode;
+  if (mode == BQC_DF_AUTO) {
+    size_t limit = o.hbm_limit;
+    if (!limit) {
+      size_t fr = 0, tot = 0;
+      BQC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+      limit = (size_t)(fr * 0.9);
+    }
+    mode = df_stored_bytes(n, naux, no, o.keep_fp32 != 0) <= limit ? BQC_DF_STORED : BQC_DF_DIRECT;
+  }
+  if (mode != BQC_DF_STORED && mode != BQC_DF_DIRECT) return BQC_E_INVALID;
+  if (o.schwarz < 0.0) o.schwarz = (mode == BQC_DF_STORED) ? 1e-12 : 1e-10;
+  if (o.aux_block <= 0) o.aux_block = 1024;
+  bqc_df *df = new (std::nothrow) bqc_df();
+  if (!df) return BQC_E_OOM;
+  df->ctx = ctx;
+  df->basis = basis;
+  df->mode = mode;
+  df->npair = npair;
+  df->opts = o;
+  auto fail = [&](int st) {
+    cudaStreamSynchronize(s);
+    delete df;
+    return st;
+  };
+  int st;
+  // metric and its Cholesky factor
+  if ((st = df->L.alloc(ctx, (size_t)naux * naux * 8)) != BQC_OK) return fail(st);
+  if ((st = launch_int2c(basis, df->L.as<double>(), s)) != BQC_OK) return fail(st);
+  if ((st = df->Vdiag.alloc(ctx, (size_t)naux * naux * 8)) != BQC_OK) return fail(st);
+  if (cudaMemcpyAsync(df->Vdiag.p, df->L.p, (size_t)naux * naux * 8, cudaMemcpyDeviceToDevice,
+                      s) != cudaSuccess)
+    return fail(BQC_E_CUDA);
+  if ((st = cholesky_lower(ctx, df->L.as<double>(), naux, s)) != BQC_OK) return fail(st);
+  if ((st = ctx->check_flag(s)) != BQC_OK) return fail(st);
+  if ((st = eri3c_plan(basis, o.schwarz, df->Vdiag.as<double>(), s, &df->plan)) != BQC_OK)
+    return fail(st);
+  if ((st = df->w.alloc(ctx, (size_t)naux * 8)) != BQC_OK) return fail(st);
+  if (mode == BQC_DF_STORED) {
+    df->Vdiag.release();  // metric only needed for the screening plan
+    if ((st = df->B64.alloc(ctx, (size_t)naux * npair * 8)) != BQC_OK) return fail(st);
+    if (cudaMemsetAsync(df->B64.p, 0, (size_t)naux * npair * 8, s) != cudaSuccess)
+      return fail(BQC_E_CUDA);
+    if ((st = launch_eri3c(basis, &df->plan, 0, naux, df->B64.as<double>(), npair, s)) != BQC_OK)
+      return fail(st);
+    if ((st = trsm_lower_left(ctx, df->L.as<double>(), naux, df->B64.as<double>(), npair, npair,
+                              s)) != BQC_OK)
+      return fail(st);
+    if ((st = df->X64.alloc(ctx, (size_t)naux * n * no * 8)) != BQC_OK) return fail(st);
+    if ((st = df->Jp.alloc(ctx, (size_t)npair * 8)) != BQC_OK) return fail(st);
+    if (o.keep_fp32) {
+      if ((st = df->B32.alloc(ctx, (size_t)naux * n * mixed_ld(n) * 4)) != BQC_OK)
+        return fail(st);
+      if ((st = df_expand_tf32(df->B64.as<double>(), n, npair, 0, naux, df->B32.as<float>(), s)) !=
+          BQC_OK)
+        return fail(st);
+      if ((st = mixed_setup(df, s)) != BQC_OK) return fail(st);
+    }
+  } else {
+    if ((st = direct_setup(df, s)) != BQC_OK) return fail(st);
+  }
+  if ((st = ctx->check_flag(s)) != BQC_OK) return fail(st);
+  *out = df;
+  return BQC_OK;
+}
+
+int bqc_df_destroy(bqc_df *df) {
+  if (!df) return BQC_E_INVALID;
+  cudaSetDevice(df->ctx->device);
+  cudaDeviceSynchronize();
+  delete df;
+  return BQC_OK;
+}
+
+int bqc_df_info(const bqc_df *df, int *mode, size_t *bytes) {
+  if (!df) return BQC_E_INVALID;
+  if (mode) *mode = df->mode;
+  if (bytes) *bytes = df->device_bytes();
+  return BQC_OK;
+}
+
+int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
+  if (!df || !out) return BQC_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int naux = df->basis->naux;
+  if (which == 0) {
+    if (df->mode != BQC_DF_STORED) return BQC_E_INVALID;
+    BQC_CUDA_TRY(cudaMemcpyAsync(out, df->B64.p, (size_t)naux * df->npair * 8,
+                                 cudaMemcpyDeviceToDevice, s));
+  } else if (which == 1) {
+    BQC_CUDA_TRY(
+        cudaMemcpyAsync(out, df->L.p, (size_t)naux * naux * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    return BQC_E_INVALID;
+  }
+  return BQC_OK;
+}
+
+int bqc_df_timing(bqc_df *df, int enable) {
+  if (!df) return BQC_E_INVALID;
+  if (enable) {
+    for (auto &e : df->ev)
+      if (!e) BQC_CUDA_TRY(cudaEventCreate(&e));
+  }
+  df->timing = enable != 0;
+  return BQC_OK;
+}
+
+int bqc_df_phase_ms(bqc_df *df, float *ms, int n) {
+  if (!df || !ms || n <= 0) return BQC_E_INVALID;
+  if (!df->timed) return BQC_E_NOT_READY;
+  BQC_CUDA_TRY(cudaEventSynchronize(df->ev[4]));
+  float t[4] = {0, 0, 0, 0}, a = 0, b = 0;
+  BQC_CUDA_TRY(cudaEventElapsedTime(&t[0], df->ev[1], df->ev[2]));
+  BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[3]));
+  BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[3], df->ev[4]));
+  BQC_CUDA_TRY(cudaEventElapsedTime(&a, df->ev[0], df->ev[1]));
+  t[3] = a + b;
+  for (int i = 0; i < n && i < 4; ++i) ms[i] = t[i];
+  return BQC_OK;
+}
+
+int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K,
+           bqc_stream_t stream) {
+  if (!df || !C || !J || !K) return BQC_E_INVALID;
+  if (nocc != df->basis->nocc) return BQC_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (df->timing) df->timed = true;
+  if (df->mode == BQC_DF_DIRECT) return jk_direct(df, C, prec, J, K, s);
+  if (prec == BQC_PREC_FP64) return jk_fp64_stored(df, C, J, K, s);
+  if (prec == BQC_PREC_MIXED_TF32) {
+    if (!df->B32.p) return BQC_E_INVALID;
+    return jk_mixed_stored(df, C, J, K, s);
+  }
+  return BQC_E_INVALID;
+}
+
+int bqc_jk_host(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K,
+                bqc_stream_t stream) {
+  if (!df || !C || !J || !K) return BQC_E_INVALID;
+  if (nocc != df->basis->nocc) return BQC_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = df->basis->nbf;
+  if (!df->host_io.p) {
+    BQC_TRY(df->host_io.alloc(df->ctx, ((size_t)n * nocc + 2 * (size_t)n * n) * 8));
+  }
+  double *dC = df->host_io.as<double>();
+  double *dJ = dC + (size_t)n * nocc, *dK = dJ + (size_t)n * n;
+  BQC_CUDA_TRY(cudaMemcpyAsync(dC, C, (size_t)n * nocc * 8, cudaMemcpyHostToDevice, s));
+  BQC_TRY(bqc_jk(df, dC, nocc, prec, dJ, dK, stream));
+  BQC_CUDA_TRY(cudaMemcpyAsync(J, dJ, (size_t)n * n * 8, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaMemcpyAsync(K, dK, (size_t)n * n * 8, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  return df->ctx->check_flag(s);
+}
+
+}  // extern "C"

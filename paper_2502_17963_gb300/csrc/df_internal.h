@@ -1,0 +1,72 @@
+// Internal state of a DF handle (stored or direct mode).
+#pragma once
+#include <memory>
+
+#include "bqc_internal.h"
+
+namespace bqc {
+
+struct MixedState;
+struct MixedDeleter {
+  void operator()(MixedState *p) const;
+};
+
+struct Df {
+  Ctx *ctx = nullptr;
+  const Basis *basis = nullptr;
+  int mode = BQC_DF_STORED;
+  int64_t npair = 0;
+  bqc_df_opts opts{};
+  DBuf L;      // Naux x Naux lower Cholesky factor of the metric
+  DBuf Vdiag;  // metric copy (screening; direct mode keeps it)
+  Eri3cPlan plan;
+  // stored mode
+  DBuf B64;    // Naux x Npair, FP64, packed lower triangle
+  DBuf X64;    // Naux x N x nocc, FP64
+  DBuf Jp;     // Npair FP64 (packed J)
+  DBuf w;      // Naux FP64: w_P = B_P : D
+  DBuf host_io;
+  // mixed precision (TF32 tensor cores)
+  DBuf B32;    // Naux x N x N, TF32-rounded FP32, full square (MMA A operand)
+  DBuf X32;    // Naux x N x nocc_pad FP32
+  DBuf Ct32;   // nocc_pad x N FP32 (C_occ^T, TF32-rounded: MMA B operand, K-major)
+  DBuf wpart;  // per X-pass tile partial w (FP64)
+  DBuf Kpart;  // SYRK partial tiles (FP32)
+  std::unique_ptr<MixedState, MixedDeleter> mixed;  // plan, tensor maps, epilogue buffers
+  // direct mode
+  DBuf raw;    // aux block x Npair FP64 raw integrals
+  DBuf raw32;  // aux block x N x N TF32 (mixed)
+  DBuf Xraw;   // Naux x N x nocc (FP64 or FP32), then Y = L^{-1} X in place
+  DBuf gamma;  // Naux FP64
+  DBuf Jacc;   // Npair FP64
+  // phase timing (bqc_df_timing)
+  bool timing = false, timed = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void mark(int i, cudaStream_t s) {
+    if (timing && ev[i]) cudaEventRecord(ev[i], s);
+  }
+  ~Df() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  size_t device_bytes() const {
+    return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +
+           wpart.n + Kpart.n + raw.n + raw32.n + Xraw.n + gamma.n + Jacc.n +
+           plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n;
+  }
+};
+
+size_t mixed_workspace_bytes(int n, int naux, int nocc);
+int mixed_ld(int n);  // row length of the TF32 shadow (N rounded up to 4)
+int mixed_setup(Df *df, cudaStream_t s);
+int jk_mixed_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
+int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
+int direct_setup(Df *df, cudaStream_t s);
+int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
+int df_expand_tf32(const double *B64, int n, int64_t npair, int p0, int np, float *B32,
+                   cudaStream_t s);
+size_t df_stored_bytes(int n, int naux, int nocc, bool fp32);
+
+}  // namespace bqc
+
+struct bqc_df : bqc::Df {};

@@ -1,0 +1,1135 @@
+// Gaussian integrals on the GPU: Boys function, Obara-Saika / Head-Gordon-Pople
+// recursions for the three-centre (P|mu nu) "Cholesky-decomposition ERIs" of
+// the density-fitted mean field (Sec. 2.2), the Coulomb metric (P|Q), the
+// Schwarz diagonals (mu nu|mu nu) and the one-electron matrices.
+//
+// Design (GB300): FP64 throughput on this part is ~1/64 of FP32, so the
+// kernels are DFMA-bound.  One shell quartet is processed by a group of G
+// lanes of a warp; each recursion level is a set of independent entries that
+// the G lanes split, with the level tables in shared memory (the paper's
+// local-memory problem for high angular momentum, Sec. 2.2.2 item 1, does not
+// arise: nothing spills).  G is chosen per class from the table size, so
+// small classes run one quartet per lane and (f|dd) runs 16-32 lanes on one.
+//
+// Recursions (Obara & Saika 1986; Head-Gordon & Pople 1988), with
+// p = a+b, q = c+d, rho = pq/(p+q), W = (pP + qQ)/(p+q):
+//   [e+1_i|f]^m = PA_i [e|f]^m + WP_i [e|f]^{m+1}
+//                 + e_i/(2p) ([e-1_i|f]^m - rho/p [e-1_i|f]^{m+1}),      (f = 0)
+//   [e|f+1_i]^m = QC_i [e|f]^m + WQ_i [e|f]^{m+1}
+//                 + f_i/(2q) ([e|f-1_i]^m - rho/q [e|f-1_i]^{m+1})
+//                 + e_i/(2(p+q)) [e-1_i|f]^{m+1},
+//   [0|0]^m = 2 pi^{5/2} / (p q sqrt(p+q)) K_ab K_cd F_m(rho |PQ|^2),
+//   (a, b+1_i| = (a+1_i, b| + AB_i (a, b|   (and likewise on the ket).
+// The three-centre integral is the case d = s with exponent 0 at C; the
+// nuclear attraction is the point-charge limit q -> infinity of the same
+// recursion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cub/cub.cuh>
+#include <type_traits>
+#include <vector>
+
+#include "bqc_internal.h"
+
+namespace bqc {
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr int ncum(int l) { return l * (l + 1) * (l + 2) / 6; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+constexpr int kCartLevels = 9;               // components for l = 0..8
+constexpr int kCartN = 165;                  // ncum(9)
+__constant__ unsigned char c_cart[kCartN][3];
+__constant__ double c_cnorm[kCartN];         // 1/sqrt((2i-1)!!(2j-1)!!(2k-1)!!)
+
+__device__ __forceinline__ int cart_index(int i, int j, int k) {
+  const int l = i + j + k, jk = j + k;
+  return ncum(l) + jk * (jk + 1) / 2 + k;
+}
+
+static void cart_tables_host(unsigned char (*cart)[3], double *cn) {
+  int n = 0;
+  for (int l = 0; l < kCartLevels; ++l)
+    for (int i = l; i >= 0; --i)
+      for (int j = l - i; j >= 0; --j) {
+        const int k = l - i - j;
+        cart[n][0] = (unsigned char)i;
+        cart[n][1] = (unsigned char)j;
+        cart[n][2] = (unsigned char)k;
+        auto df = [](int m) {
+          double r = 1.0;
+          for (int t = 2 * m - 1; t > 1; t -= 2) r *= t;
+          return r;
+        };
+        cn[n] = 1.0 / std::sqrt(df(i) * df(j) * df(k));
+        ++n;
+      }
+}
+
+static int upload_cart_tables() {
+  static std::once_flag once;
+  static int status = BQC_OK;
+  std::call_once(once, [] {
+    unsigned char cart[kCartN][3];
+    double cn[kCartN];
+    cart_tables_host(cart, cn);
+    if (cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)) != cudaSuccess ||
+        cudaMemcpyToSymbol(c_cnorm, cn, sizeof(cn)) != cudaSuccess)
+      status = BQC_E_CUDA;
+  });
+  return status;
+}
+
+// ------------------------------------------------------------ Boys -------
+
+// F_m(T) at the grid points from the power series
+// F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)), summed in long
+// double; the device evaluates F_m by an 8-term Taylor expansion about the
+// nearest grid point (dF_m/dT = -F_{m+1}), and for T >= 36 by
+// F_0 = sqrt(pi/T)/2 with the upward recursion F_{m+1} = ((2m+1)F_m - e^{-T})/(2T).
+int boys_table_build(Ctx *ctx) {
+  std::vector<double> tab((size_t)kBoysNT * kBoysNM);
+  for (int k = 0; k < kBoysNT; ++k) {
+    const long double T = (long double)k * kBoysH;
+    for (int m = 0; m < kBoysNM; ++m) {
+      long double den = 2.0L * m + 1.0L, term = 1.0L / den, sum = term;
+      for (int t = 1; t < 4000; ++t) {
+        term *= 2.0L * T / (den + 2.0L * t);
+        sum += term;
+        if (term < 1e-22L * sum) break;
+      }
+      tab[(size_t)k * kBoysNM + m] = (double)(expl(-T) * sum);
+    }
+  }
+  void *p = ctx->dmalloc(tab.size() * sizeof(double));
+  if (!p) return BQC_E_OOM;
+  ctx->boys = (double *)p;
+  BQC_CUDA_TRY(cudaMemcpy(ctx->boys, tab.data(), tab.size() * sizeof(double),
+                          cudaMemcpyHostToDevice));
+  return upload_cart_tables();
+}
+
+__device__ __forceinline__ double boys_one(const double *__restrict__ tab, int m, double T,
+                                           double expmT_large) {
+  if (T < kBoysTCut) {
+    const int k = __double2int_rn(T * (1.0 / kBoysH));
+    const double d = -(T - k * kBoysH);
+    const double *row = tab + (size_t)k * kBoysNM + m;
+    // sum_j F_{m+j}(T_k) d^j / j!  (Horner)
+    double r = __ldg(row + 7) * (1.0 / 5040.0);
+    r = fma(r, d, __ldg(row + 6) * (1.0 / 720.0));
+    r = fma(r, d, __ldg(row + 5) * (1.0 / 120.0));
+    r = fma(r, d, __ldg(row + 4) * (1.0 / 24.0));
+    r = fma(r, d, __ldg(row + 3) * (1.0 / 6.0));
+    r = fma(r, d, __ldg(row + 2) * 0.5);
+    r = fma(r, d, __ldg(row + 1));
+    r = fma(r, d, __ldg(row + 0));
+    return r;
+  }
+  const double inv2T = 0.5 / T;
+  double f = 0.5 * sqrt(3.141592653589793 / T);
+  for (int j = 0; j < m; ++j) f = ((2 * j + 1) * f - expmT_large) * inv2T;
+  return f;
+}
+
+__global__ void k_boys_eval(const double *__restrict__ tab, int n, const double *__restrict__ T,
+                            int mmax, double *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * (mmax + 1)) return;
+  const int64_t t = i / (mmax + 1);
+  const int m = (int)(i - t * (mmax + 1));
+  const double x = T[t];
+  const double e = x >= kBoysTCut ? exp(-x) : 0.0;
+  out[i] = boys_one(tab, m, x, e);
+}
+
+int launch_boys_eval(Ctx *ctx, int n, const double *T, int mmax, double *out, cudaStream_t s) {
+  if (n < 0 || mmax < 0 || mmax > kBoysMaxM) return BQC_E_INVALID;
+  if (n == 0) return BQC_OK;
+  const int64_t tot = (int64_t)n * (mmax + 1);
+  k_boys_eval<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->boys, n, T, mmax, out);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+// --------------------------------------------------- OS/HGP engine -------
+
+template <int I, int N, class Fn>
+__device__ __forceinline__ void static_for(Fn &&fn) {
+  if constexpr (I < N) {
+    fn(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(fn);
+  }
+}
+
+// Table geometry of one class (all sizes in doubles).
+template <int LA, int LB, int LC, int LD>
+struct Os {
+  static constexpr int E = LA + LB, F = LC + LD, L = E + F;
+  static constexpr int NE = ncum(E + 1);
+  static constexpr int S1 = NE * (L + 1);  // [e][m], m <= L - |e|
+  __host__ __device__ static constexpr int elo(int f) { return cmax(LA - (F - f), 0); }
+  __host__ __device__ static constexpr int lne(int f) { return NE - ncum(elo(f)); }
+  __host__ __device__ static constexpr int lm(int f) { return F - f + 1; }
+  __host__ __device__ static constexpr int lsz(int f) { return lne(f) * ncart(f) * lm(f); }
+  __host__ __device__ static constexpr int loff(int f) {
+    int o = 0;
+    for (int g = 1; g < f; ++g) o += lsz(g);
+    return o;
+  }
+  static constexpr int GSZ = loff(F + 1);
+  static constexpr int NEA = NE - ncum(LA);
+  static constexpr int NFC = ncum(F + 1) - ncum(LC);
+  static constexpr int ACC = NEA * NFC;
+  static constexpr int NAB = ncart(LA) * ncart(LB);
+  __host__ __device__ static constexpr int hbsz(int j) {
+    return (ncum(E - j + 1) - ncum(LA)) * ncart(j) * NFC;
+  }
+  __host__ __device__ static constexpr int hksz(int j) {
+    return NAB * (ncum(F - j + 1) - ncum(LC)) * ncart(j);
+  }
+  __host__ __device__ static constexpr int hmax() {
+    int m = 0;
+    for (int j = 1; j <= LB; ++j) m = cmax(m, hbsz(j));
+    for (int j = 1; j <= LD; ++j) m = cmax(m, hksz(j));
+    return m;
+  }
+  static constexpr int HMAX = hmax();
+  static constexpr int NOUT = NAB * ncart(LC) * ncart(LD);
+  static constexpr int PH1 = S1 + GSZ;
+  static constexpr int PH2 = 2 * HMAX;
+  static constexpr int SCR = ACC + cmax(PH1, PH2);
+  // lanes per quartet: keep <= ~96 doubles of table per lane
+  static constexpr int lanes() {
+    int g = 1;
+    while (g < 32 && SCR > 96 * g) g *= 2;
+    return g;
+  }
+  static constexpr int G = lanes();
+};
+
+// Scalars of one primitive quartet.
+struct PrimQ {
+  double PA[3], WP[3], QC[3], WQ[3];
+  double inv2p, rho_p, inv2q, rho_q, inv2pq, T, pref;
+};
+
+// Geometry of a primitive quartet (a,b|c,d).  point != 0: ket is a point
+// charge at C (nuclear attraction): rho = p, W = C, prefactor 2 pi / p.
+__device__ __forceinline__ void prim_setup(double a, const double *A, double b, const double *B,
+                                           double c, const double *C, double d, const double *D,
+                                           double cabcd, int point, PrimQ &g) {
+  const double p = a + b, ip = 1.0 / p;
+  double P[3], AB2 = 0.0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    P[x] = (a * A[x] + b * B[x]) * ip;
+    const double t = A[x] - B[x];
+    AB2 += t * t;
+    g.PA[x] = P[x] - A[x];
+  }
+  const double Kab = exp(-a * b * ip * AB2);
+  if (point) {
+    double PC2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const double t = C[x] - P[x];
+      g.WP[x] = t;
+      PC2 += t * t;
+      g.QC[x] = 0.0;
+      g.WQ[x] = 0.0;
+    }
+    g.inv2p = 0.5 * ip;
+    g.rho_p = 1.0;
+    g.inv2q = g.rho_q = g.inv2pq = 0.0;
+    g.T = p * PC2;
+    g.pref = 2.0 * 3.141592653589793 * ip * Kab * cabcd;
+    return;
+  }
+  const double q = c + d, iq = 1.0 / q;
+  double Q[3], CD2 = 0.0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    Q[x] = (c * C[x] + d * D[x]) * iq;
+    const double t = C[x] - D[x];
+    CD2 += t * t;
+    g.QC[x] = Q[x] - C[x];
+  }
+  const double Kcd = (d == 0.0) ? 1.0 : exp(-c * d * iq * CD2);
+  const double ipq = 1.0 / (p + q);
+  const double rho = p * q * ipq;
+  double PQ2 = 0.0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const double W = (p * P[x] + q * Q[x]) * ipq;
+    g.WP[x] = W - P[x];
+    g.WQ[x] = W - Q[x];
+    const double t = P[x] - Q[x];
+    PQ2 += t * t;
+  }
+  g.inv2p = 0.5 * ip;
+  g.rho_p = rho * ip;
+  g.inv2q = 0.5 * iq;
+  g.rho_q = rho * iq;
+  g.inv2pq = 0.5 * ipq;
+  g.T = rho * PQ2;
+  // 2 pi^{5/2} = 34.98683665524972
+  g.pref = 34.98683665524972 * ip * iq * sqrt(ipq) * Kab * Kcd * cabcd;
+}
+
+__device__ __forceinline__ int first_dir(const unsigned char *n) {
+  return n[0] > 0 ? 0 : (n[1] > 0 ? 1 : 2);
+}
+
+// VRR for one primitive quartet and accumulation into acc.  Group-cooperative:
+// lane gl of G.  scr: S1 table then ket levels.  The caller syncs after.
+template <int LA, int LB, int LC, int LD, int G>
+__device__ __forceinline__ void os_vrr_accumulate(const PrimQ &g, const double *__restrict__ boys,
+                                                  double *__restrict__ acc,
+                                                  double *__restrict__ s1,
+                                                  double *__restrict__ gk, int gl) {
+  using O = Os<LA, LB, LC, LD>;
+  constexpr int L = O::L, E = O::E, F = O::F;
+  // level 0: [0|0]^m
+  {
+    const double e = g.T >= kBoysTCut ? exp(-g.T) : 0.0;
+    for (int m = gl; m <= L; m += G) s1[m] = g.pref * boys_one(boys, m, g.T, e);
+  }
+  __syncwarp();
+  // bra levels e = 1..E on f = 0
+  static_for<1, E + 1>([&](auto ei) {
+    constexpr int e = decltype(ei)::value;
+    constexpr int M = L - e + 1;
+    constexpr int CNT = ncart(e) * M;
+    for (int idx = gl; idx < CNT; idx += G) {
+      const int c = idx / M, m = idx - c * M;
+      const int ci = ncum(e) + c;
+      const unsigned char *n = c_cart[ci];
+      const int d = first_dir(n);
+      const int nd = n[d];
+      int i1[3] = {n[0], n[1], n[2]};
+      i1[d] -= 1;
+      const int e1 = cart_index(i1[0], i1[1], i1[2]);
+      double v = g.PA[d] * s1[e1 * (L + 1) + m] + g.WP[d] * s1[e1 * (L + 1) + m + 1];
+      if (nd >= 2) {
+        i1[d] -= 1;
+        const int e2 = cart_index(i1[0], i1[1], i1[2]);
+        v += (nd - 1) * g.inv2p * (s1[e2 * (L + 1) + m] - g.rho_p * s1[e2 * (L + 1) + m + 1]);
+      }
+      s1[ci * (L + 1) + m] = v;
+    }
+    __syncwarp();
+  });
+  // ket levels f = 1..F
+  auto get = [&](auto lvl, int ecum, int fc, int m) -> double {
+    constexpr int gg = decltype(lvl)::value;
+    if constexpr (gg == 0) {
+      return s1[ecum * (L + 1) + m];
+    } else {
+      return gk[O::loff(gg) + ((ecum - ncum(O::elo(gg))) * ncart(gg) + fc) * O::lm(gg) + m];
+    }
+  };
+  static_for<1, F + 1>([&](auto fi) {
+    constexpr int f = decltype(fi)::value;
+    constexpr int LM = O::lm(f), NF = ncart(f);
+    constexpr int CNT = O::lne(f) * NF * LM;
+    for (int idx = gl; idx < CNT; idx += G) {
+      const int m = idx % LM;
+      const int t = idx / LM;
+      const int fc = t % NF, er = t / NF;
+      const int ecum = ncum(O::elo(f)) + er;
+      const unsigned char *ne = c_cart[ecum];
+      const unsigned char *nf = c_cart[ncum(f) + fc];
+      const int d = first_dir(nf);
+      const int nd = nf[d];
+      int j1[3] = {nf[0], nf[1], nf[2]};
+      j1[d] -= 1;
+      const int f1 = cart_index(j1[0], j1[1], j1[2]) - ncum(f - 1);
+      std::integral_constant<int, f - 1> lv1;
+      double v = g.QC[d] * get(lv1, ecum, f1, m) + g.WQ[d] * get(lv1, ecum, f1, m + 1);
+      if constexpr (f >= 2) {
+        if (nd >= 2) {
+          j1[d] -= 1;
+          const int f2 = cart_index(j1[0], j1[1], j1[2]) - ncum(f - 2);
+          std::integral_constant<int, f - 2> lv2;
+          v += (nd - 1) * g.inv2q * (get(lv2, ecum, f2, m) - g.rho_q * get(lv2, ecum, f2, m + 1));
+        }
+      }
+      const int ed = ne[d];
+      if (ed >= 1) {
+        int i1[3] = {ne[0], ne[1], ne[2]};
+        i1[d] -= 1;
+        const int e1 = cart_index(i1[0], i1[1], i1[2]);
+        v += ed * g.inv2pq * get(lv1, e1, f1, m + 1);
+      }
+      gk[O::loff(f) + (er * NF + fc) * LM + m] = v;
+    }
+    __syncwarp();
+  });
+  // accumulate [e|f]^0 for e in [LA, E], f in [LC, F]
+  static_for<LC, F + 1>([&](auto fi) {
+    constexpr int f = decltype(fi)::value;
+    constexpr int NF = ncart(f);
+    constexpr int CNT = O::NEA * NF;
+    for (int idx = gl; idx < CNT; idx += G) {
+      const int fc = idx % NF, er = idx / NF;
+      const int ecum = ncum(LA) + er;
+      acc[er * O::NFC + (ncum(f) - ncum(LC)) + fc] += get(fi, ecum, fc, 0);
+    }
+  });
+  __syncwarp();
+}
+
+// Horizontal recursions after the primitive loops.  Returns the table holding
+// [ab][c][d] (layout (a*nb + b) * nc * nd + c * nd + d).
+template <int LA, int LB, int LC, int LD, int G>
+__device__ __forceinline__ const double *os_hrr(const double *acc, double *bufA, double *bufB,
+                                                int gl, const double *AB, const double *CD) {
+  using O = Os<LA, LB, LC, LD>;
+  constexpr int E = O::E, F = O::F, NFC = O::NFC;
+  const double *src = acc;
+  double *dst = bufA;
+  static_for<1, LB + 1>([&](auto ji) {
+    constexpr int j = decltype(ji)::value;
+    constexpr int NB = ncart(j), NBP = ncart(j - 1);
+    constexpr int CNT = (ncum(E - j + 1) - ncum(LA)) * NB * NFC;
+    for (int idx = gl; idx < CNT; idx += G) {
+      const int fr = idx % NFC;
+      const int t = idx / NFC;
+      const int bc = t % NB, ar = t / NB;
+      const unsigned char *na = c_cart[ncum(LA) + ar];
+      const unsigned char *nb = c_cart[ncum(j) + bc];
+      const int d = first_dir(nb);
+      int b1[3] = {nb[0], nb[1], nb[2]};
+      b1[d] -= 1;
+      const int bp = cart_index(b1[0], b1[1], b1[2]) - ncum(j - 1);
+      int a1[3] = {na[0], na[1], na[2]};
+      a1[d] += 1;
+      const int a1r = cart_index(a1[0], a1[1], a1[2]) - ncum(LA);
+      dst[(ar * NB + bc) * NFC + fr] =
+          src[(a1r * NBP + bp) * NFC + fr] + AB[d] * src[(ar * NBP + bp) * NFC + fr];
+    }
+    __syncwarp();
+    src = dst;
+    dst = (dst == bufA) ? bufB : bufA;
+  });
+  static_for<1, LD + 1>([&](auto ji) {
+    constexpr int j = decltype(ji)::value;
+    constexpr int ND = ncart(j), NDP = ncart(j - 1);
+    constexpr int NCJ = ncum(F - j + 1) - ncum(LC), NCP = ncum(F - j + 2) - ncum(LC);
+    constexpr int CNT = O::NAB * NCJ * ND;
+    for (int idx = gl; idx < CNT; idx += G) {
+      const int dc = idx % ND;
+      const int t = idx / ND;
+      const int cr = t % NCJ, ab = t / NCJ;
+      const unsigned char *nc = c_cart[ncum(LC) + cr];
+      const unsigned char *nd = c_cart[ncum(j) + dc];
+      const int d = first_dir(nd);
+      int d1[3] = {nd[0], nd[1], nd[2]};
+      d1[d] -= 1;
+      const int dp = cart_index(d1[0], d1[1], d1[2]) - ncum(j - 1);
+      int c1[3] = {nc[0], nc[1], nc[2]};
+      c1[d] += 1;
+      const int c1r = cart_index(c1[0], c1[1], c1[2]) - ncum(LC);
+      dst[(ab * NCJ + cr) * ND + dc] =
+          src[(ab * NCP + c1r) * NDP + dp] + CD[d] * src[(ab * NCP + cr) * NDP + dp];
+    }
+    __syncwarp();
+    src = dst;
+    dst = (dst == bufA) ? bufB : bufA;
+  });
+  return src;
+}
+
+struct ShellRef {
+  int l, nprim, poff, fn;
+  double xyz[3];
+};
+
+__device__ __forceinline__ ShellRef load_shell(const ShellSetDev &s, int i) {
+  ShellRef r;
+  r.l = s.l[i];
+  r.nprim = s.nprim[i];
+  r.poff = s.poff[i];
+  r.fn = s.fn[i];
+  r.xyz[0] = s.xyz[3 * i];
+  r.xyz[1] = s.xyz[3 * i + 1];
+  r.xyz[2] = s.xyz[3 * i + 2];
+  return r;
+}
+
+// One quartet (a b|c d) by a group; d may be "unit" (exponent 0 at C) and b
+// may be unit too.  Result via os_hrr.
+template <int LA, int LB, int LC, int LD, int G>
+__device__ __forceinline__ const double *os_quartet(
+    const double *boys, double *scr, int gl, const ShellRef &sa, const double *ea,
+    const double *ca, const ShellRef *sb, const double *eb, const double *cb, const ShellRef &sc,
+    const double *ec, const double *cc, const ShellRef *sd, const double *ed, const double *cd) {
+  using O = Os<LA, LB, LC, LD>;
+  double *acc = scr;
+  double *s1 = scr + O::ACC;
+  double *gk = s1 + O::S1;
+  for (int i = gl; i < O::ACC; i += G) acc[i] = 0.0;
+  __syncwarp();
+  const double *B = sb ? sb->xyz : sa.xyz;
+  const double *D = sd ? sd->xyz : sc.xyz;
+  const int nb = sb ? sb->nprim : 1, nd = sd ? sd->nprim : 1;
+  for (int ia = 0; ia < sa.nprim; ++ia)
+    for (int ib = 0; ib < nb; ++ib)
+      for (int ic = 0; ic < sc.nprim; ++ic)
+        for (int id = 0; id < nd; ++id) {
+          PrimQ g;
+          const double xb = sb ? eb[ib] : 0.0, wb = sb ? cb[ib] : 1.0;
+          const double xd = sd ? ed[id] : 0.0, wd = sd ? cd[id] : 1.0;
+          prim_setup(ea[ia], sa.xyz, xb, B, ec[ic], sc.xyz, xd, D, ca[ia] * wb * cc[ic] * wd, 0,
+                     g);
+          os_vrr_accumulate<LA, LB, LC, LD, G>(g, boys, acc, s1, gk, gl);
+        }
+  double AB[3], CD[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    AB[x] = sa.xyz[x] - B[x];
+    CD[x] = sc.xyz[x] - D[x];
+  }
+  double *bufA = scr + O::ACC;
+  double *bufB = bufA + O::HMAX;
+  return os_hrr<LA, LB, LC, LD, G>(acc, bufA, bufB, gl, AB, CD);
+}
+
+// ------------------------------------------------ three-centre kernel ----
+
+struct Eri3cArgs {
+  ShellSetDev orb, aux;
+  const double *boys;
+  const int2 *pairs;       // class segment, sorted by Schwarz factor
+  const int *aux_list;     // aux shells of this l
+  const int64_t *prefix;   // n_aux + 1 survivor prefix
+  int n_aux;
+  int p0, p1;              // aux function window [p0, p1)
+  double *out;
+  int64_t ld;
+  int *flag;
+  int64_t out_elems;
+};
+
+template <int LC, int LA, int LB>
+__global__ void __launch_bounds__(256) k_eri3c(Eri3cArgs a) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G;
+  const int group_in_block = threadIdx.x / G;
+  const int groups_per_block = blockDim.x / G;
+  double *scr = smem + (size_t)group_in_block * O::SCR;
+  const int64_t total = a.prefix[a.n_aux];
+  const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
+  // warp-uniform trip count: all groups of a warp iterate together
+  const int warp_first_group = (threadIdx.x >> 5) * (32 / G);
+  const int64_t base0 = (int64_t)blockIdx.x * groups_per_block + warp_first_group;
+  for (int64_t base = base0; base < total; base += gstride) {
+    int64_t t = base + (group_in_block - warp_first_group);
+    const bool active = t < total;
+    if (!active) t = total - 1;
+    // aux shell: largest i with prefix[i] <= t
+    int lo = 0, hi = a.n_aux;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.prefix[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int Pi = a.aux_list[lo];
+    const int2 pr = a.pairs[t - a.prefix[lo]];
+    const ShellRef sc = load_shell(a.aux, Pi);
+    const ShellRef sa = load_shell(a.orb, pr.x);
+    const ShellRef sb = load_shell(a.orb, pr.y);
+    const double *res = os_quartet<LA, LB, LC, 0, G>(
+        a.boys, scr, gl, sa, a.orb.exps + sa.poff, a.orb.coefs + sa.poff, &sb,
+        a.orb.exps + sb.poff, a.orb.coefs + sb.poff, sc, a.aux.exps + sc.poff,
+        a.aux.coefs + sc.poff, nullptr, nullptr, nullptr);
+    if (active) {
+      constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC);
+      const bool diag = pr.x == pr.y;
+      for (int idx = gl; idx < O::NOUT; idx += G) {
+        const int ic = idx % NC;
+        const int ab = idx / NC;
+        const int ib = ab % NB, ia = ab / NB;
+        const int P = sc.fn + ic;
+        if (P < a.p0 || P >= a.p1) continue;
+        int mu = sa.fn + ia, nu = sb.fn + ib;
+        if (diag && mu < nu) continue;
+        if (mu < nu) { const int t2 = mu; mu = nu; nu = t2; }
+        const int64_t col = (int64_t)mu * (mu + 1) / 2 + nu;
+        const int64_t o = (int64_t)(P - a.p0) * a.ld + col;
+        if (o < 0 || o >= a.out_elems) { atomicExch(a.flag, 3); continue; }
+        a.out[o] = res[idx] * c_cnorm[ncum(LA) + ia] * c_cnorm[ncum(LB) + ib] *
+                   c_cnorm[ncum(LC) + ic];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int LC, int LA, int LB>
+static int launch3(const Eri3cArgs &a, int64_t total, cudaStream_t s) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G;
+  // groups per block: up to 256 threads and ~196 KB of tables
+  int groups = 256 / G;
+  while (groups > 32 / G && (size_t)groups * O::SCR * 8 > 196 * 1024) groups -= 32 / G;
+  const size_t smem = (size_t)groups * O::SCR * 8;
+  if (smem > 227 * 1024) return BQC_E_UNSUPPORTED;
+  auto kern = k_eri3c<LC, LA, LB>;
+  BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int64_t blocks = (total + groups - 1) / groups;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+template <int LC>
+static int dispatch3_pair(int cls, const Eri3cArgs &a, int64_t total, cudaStream_t s) {
+  switch (cls) {
+    case 0: return launch3<LC, 0, 0>(a, total, s);
+    case 1: return launch3<LC, 1, 0>(a, total, s);
+    case 2: return launch3<LC, 1, 1>(a, total, s);
+    case 3: return launch3<LC, 2, 0>(a, total, s);
+    case 4: return launch3<LC, 2, 1>(a, total, s);
+    case 5: return launch3<LC, 2, 2>(a, total, s);
+  }
+  return BQC_E_UNSUPPORTED;
+}
+
+static int dispatch3(int lc, int cls, const Eri3cArgs &a, int64_t total, cudaStream_t s) {
+  switch (lc) {
+    case 0: return dispatch3_pair<0>(cls, a, total, s);
+    case 1: return dispatch3_pair<1>(cls, a, total, s);
+    case 2: return dispatch3_pair<2>(cls, a, total, s);
+    case 3: return dispatch3_pair<3>(cls, a, total, s);
+  }
+  return BQC_E_UNSUPPORTED;
+}
+
+int launch_eri3c(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *out, int64_t ld,
+                 cudaStream_t s) {
+  if (p0 < 0 || p1 > b->naux || p0 > p1) return BQC_E_INVALID;
+  if (p0 == p1) return BQC_OK;
+  for (int lc = 0; lc <= kMaxLAux; ++lc) {
+    const int na = b->auxl_off[lc + 1] - b->auxl_off[lc];
+    if (na == 0) continue;
+    for (int cls = 0; cls < kNPairClass; ++cls) {
+      const int np = b->pair_off[cls + 1] - b->pair_off[cls];
+      if (np == 0 || plan->total[cls][lc] == 0) continue;
+      Eri3cArgs a;
+      a.orb = b->orb.dev;
+      a.aux = b->aux.dev;
+      a.boys = b->ctx->boys;
+      a.pairs = plan->d_pairs_sorted.as<int2>() + b->pair_off[cls];
+      a.aux_list = b->d_aux_by_l.as<int>() + b->auxl_off[lc];
+      a.prefix = plan->d_prefix.as<int64_t>() + plan->prefix_off[cls][lc];
+      a.n_aux = na;
+      a.p0 = p0;
+      a.p1 = p1;
+      a.out = out;
+      a.ld = ld;
+      a.flag = b->ctx->flag;
+      a.out_elems = (int64_t)(p1 - p0) * ld;
+      BQC_TRY(dispatch3(lc, cls, a, plan->total[cls][lc], s));
+    }
+  }
+  return BQC_OK;
+}
+
+// ------------------------------------------------------ Schwarz kernel ---
+
+struct SchwarzArgs {
+  ShellSetDev orb;
+  const double *boys;
+  const int2 *pairs;
+  int npair;
+  double *Q;
+};
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256) k_schwarz(SchwarzArgs a) {
+  using O = Os<LA, LB, LA, LB>;
+  constexpr int G = O::G;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  const int gib = threadIdx.x / G, gpb = blockDim.x / G;
+  double *scr = smem + (size_t)gib * O::SCR;
+  const int wfg = (threadIdx.x >> 5) * (32 / G);
+  for (int64_t base = (int64_t)blockIdx.x * gpb + wfg; base < a.npair;
+       base += (int64_t)gridDim.x * gpb) {
+    int64_t t = base + (gib - wfg);
+    const bool active = t < a.npair;
+    if (!active) t = a.npair - 1;
+    const int2 pr = a.pairs[t];
+    const ShellRef sa = load_shell(a.orb, pr.x), sb = load_shell(a.orb, pr.y);
+    const double *ea = a.orb.exps + sa.poff, *ca = a.orb.coefs + sa.poff;
+    const double *eb = a.orb.exps + sb.poff, *cb = a.orb.coefs + sb.poff;
+    const double *res =
+        os_quartet<LA, LB, LA, LB, G>(a.boys, scr, gl, sa, ea, ca, &sb, eb, cb, sa, ea, ca, &sb,
+                                      eb, cb);
+    if (active && gl == 0) {
+      constexpr int NA = ncart(LA), NB = ncart(LB);
+      double mx = 0.0;
+      for (int ia = 0; ia < NA; ++ia)
+        for (int ib = 0; ib < NB; ++ib) {
+          const double n = c_cnorm[ncum(LA) + ia] * c_cnorm[ncum(LB) + ib];
+          const double v = res[((ia * NB + ib) * NA + ia) * NB + ib] * n * n;
+          mx = fmax(mx, fabs(v));
+        }
+      a.Q[t] = sqrt(mx);
+    }
+    __syncwarp();
+  }
+}
+
+template <int LA, int LB>
+static int launch_schwarz_cls(const SchwarzArgs &a, cudaStream_t s) {
+  using O = Os<LA, LB, LA, LB>;
+  constexpr int G = O::G;
+  int groups = 256 / G;
+  while (groups > 32 / G && (size_t)groups * O::SCR * 8 > 196 * 1024) groups -= 32 / G;
+  const size_t smem = (size_t)groups * O::SCR * 8;
+  if (smem > 227 * 1024) return BQC_E_UNSUPPORTED;
+  auto kern = k_schwarz<LA, LB>;
+  BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int64_t blocks = (a.npair + groups - 1) / groups;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int launch_schwarz_pairs(const Basis *b, double *Qpair, cudaStream_t s) {
+  for (int cls = 0; cls < kNPairClass; ++cls) {
+    const int np = b->pair_off[cls + 1] - b->pair_off[cls];
+    if (np == 0) continue;
+    SchwarzArgs a;
+    a.orb = b->orb.dev;
+    a.boys = b->ctx->boys;
+    a.pairs = b->d_pairs.as<int2>() + b->pair_off[cls];
+    a.npair = np;
+    a.Q = Qpair + b->pair_off[cls];
+    int st = BQC_E_UNSUPPORTED;
+    switch (cls) {
+      case 0: st = launch_schwarz_cls<0, 0>(a, s); break;
+      case 1: st = launch_schwarz_cls<1, 0>(a, s); break;
+      case 2: st = launch_schwarz_cls<1, 1>(a, s); break;
+      case 3: st = launch_schwarz_cls<2, 0>(a, s); break;
+      case 4: st = launch_schwarz_cls<2, 1>(a, s); break;
+      case 5: st = launch_schwarz_cls<2, 2>(a, s); break;
+    }
+    BQC_TRY(st);
+  }
+  return BQC_OK;
+}
+
+// ------------------------------------------------------- metric (P|Q) ----
+
+struct Int2cArgs {
+  ShellSetDev aux;
+  const double *boys;
+  const int *listP, *listQ;
+  int nP, nQ;
+  double *V;
+  int naux;
+};
+
+template <int LP, int LQ>
+__global__ void __launch_bounds__(256) k_int2c(Int2cArgs a) {
+  using O = Os<LP, 0, LQ, 0>;
+  constexpr int G = O::G;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  const int gib = threadIdx.x / G, gpb = blockDim.x / G;
+  double *scr = smem + (size_t)gib * O::SCR;
+  const int wfg = (threadIdx.x >> 5) * (32 / G);
+  const int64_t total = (int64_t)a.nP * a.nQ;
+  for (int64_t base = (int64_t)blockIdx.x * gpb + wfg; base < total;
+       base += (int64_t)gridDim.x * gpb) {
+    int64_t t = base + (gib - wfg);
+    const bool active = t < total;
+    if (!active) t = total - 1;
+    const int iP = a.listP[t / a.nQ], iQ = a.listQ[t % a.nQ];
+    const ShellRef sp = load_shell(a.aux, iP), sq = load_shell(a.aux, iQ);
+    const double *res = os_quartet<LP, 0, LQ, 0, G>(
+        a.boys, scr, gl, sp, a.aux.exps + sp.poff, a.aux.coefs + sp.poff, nullptr, nullptr,
+        nullptr, sq, a.aux.exps + sq.poff, a.aux.coefs + sq.poff, nullptr, nullptr, nullptr);
+    if (active) {
+      constexpr int NP = ncart(LP), NQ = ncart(LQ);
+      for (int idx = gl; idx < NP * NQ; idx += G) {
+        const int iq = idx % NQ, ip = idx / NQ;
+        a.V[(int64_t)(sp.fn + ip) * a.naux + sq.fn + iq] =
+            res[idx] * c_cnorm[ncum(LP) + ip] * c_cnorm[ncum(LQ) + iq];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int LP, int LQ>
+static int launch_int2c_cls(const Int2cArgs &a, cudaStream_t s) {
+  using O = Os<LP, 0, LQ, 0>;
+  constexpr int G = O::G;
+  int groups = 256 / G;
+  while (groups > 32 / G && (size_t)groups * O::SCR * 8 > 196 * 1024) groups -= 32 / G;
+  const size_t smem = (size_t)groups * O::SCR * 8;
+  auto kern = k_int2c<LP, LQ>;
+  BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  const int64_t total = (int64_t)a.nP * a.nQ;
+  int64_t blocks = (total + groups - 1) / groups;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+template <int LP>
+static int int2c_q(int lq, const Int2cArgs &a, cudaStream_t s) {
+  switch (lq) {
+    case 0: return launch_int2c_cls<LP, 0>(a, s);
+    case 1: return launch_int2c_cls<LP, 1>(a, s);
+    case 2: return launch_int2c_cls<LP, 2>(a, s);
+    case 3: return launch_int2c_cls<LP, 3>(a, s);
+  }
+  return BQC_E_UNSUPPORTED;
+}
+
+int launch_int2c(const Basis *b, double *V, cudaStream_t s) {
+  for (int lp = 0; lp <= kMaxLAux; ++lp)
+    for (int lq = 0; lq <= kMaxLAux; ++lq) {
+      const int nP = b->auxl_off[lp + 1] - b->auxl_off[lp];
+      const int nQ = b->auxl_off[lq + 1] - b->auxl_off[lq];
+      if (!nP || !nQ) continue;
+      Int2cArgs a;
+      a.aux = b->aux.dev;
+      a.boys = b->ctx->boys;
+      a.listP = b->d_aux_by_l.as<int>() + b->auxl_off[lp];
+      a.listQ = b->d_aux_by_l.as<int>() + b->auxl_off[lq];
+      a.nP = nP;
+      a.nQ = nQ;
+      a.V = V;
+      a.naux = b->naux;
+      int st = BQC_E_UNSUPPORTED;
+      switch (lp) {
+        case 0: st = int2c_q<0>(lq, a, s); break;
+        case 1: st = int2c_q<1>(lq, a, s); break;
+        case 2: st = int2c_q<2>(lq, a, s); break;
+        case 3: st = int2c_q<3>(lq, a, s); break;
+      }
+      BQC_TRY(st);
+    }
+  return BQC_OK;
+}
+
+// -------------------------------------------------- one-electron parts ---
+
+struct OneArgs {
+  ShellSetDev orb;
+  const double *boys;
+  const int2 *pairs;
+  int npair;
+  const double *atoms;  // natom x 4 (x, y, z, Z)
+  int natom;
+  double *S, *T, *V;
+  int nbf;
+};
+
+// Nuclear attraction: point-charge limit of the OS recursion, summed over
+// nuclei (Obara & Saika 1986: [a+1_i]^m = PA_i [a]^m - PC_i [a]^{m+1} + ...).
+template <int LA, int LB>
+__global__ void __launch_bounds__(256) k_nuclear(OneArgs a) {
+  using O = Os<LA, LB, 0, 0>;
+  constexpr int G = O::G;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  const int gib = threadIdx.x / G, gpb = blockDim.x / G;
+  double *scr = smem + (size_t)gib * O::SCR;
+  const int wfg = (threadIdx.x >> 5) * (32 / G);
+  for (int64_t base = (int64_t)blockIdx.x * gpb + wfg; base < a.npair;
+       base += (int64_t)gridDim.x * gpb) {
+    int64_t t = base + (gib - wfg);
+    const bool active = t < a.npair;
+    if (!active) t = a.npair - 1;
+    const int2 pr = a.pairs[t];
+    const ShellRef sa = load_shell(a.orb, pr.x), sb = load_shell(a.orb, pr.y);
+    const double *ea = a.orb.exps + sa.poff, *ca = a.orb.coefs + sa.poff;
+    const double *eb = a.orb.exps + sb.poff, *cb = a.orb.coefs + sb.poff;
+    double *acc = scr;
+    double *s1 = scr + O::ACC;
+    for (int i = gl; i < O::ACC; i += G) acc[i] = 0.0;
+    __syncwarp();
+    for (int n = 0; n < a.natom; ++n) {
+      const double C[3] = {a.atoms[4 * n], a.atoms[4 * n + 1], a.atoms[4 * n + 2]};
+      const double Z = a.atoms[4 * n + 3];
+      for (int ia = 0; ia < sa.nprim; ++ia)
+        for (int ib = 0; ib < sb.nprim; ++ib) {
+          PrimQ g;
+          prim_setup(ea[ia], sa.xyz, eb[ib], sb.xyz, 0.0, C, 0.0, C, -Z * ca[ia] * cb[ib], 1, g);
+          os_vrr_accumulate<LA, LB, 0, 0, G>(g, a.boys, acc, s1, nullptr, gl);
+        }
+    }
+    double AB[3], CD[3] = {0.0, 0.0, 0.0};
+    for (int x = 0; x < 3; ++x) AB[x] = sa.xyz[x] - sb.xyz[x];
+    double *bufA = scr + O::ACC;
+    double *bufB = bufA + O::HMAX;
+    const double *res = os_hrr<LA, LB, 0, 0, G>(acc, bufA, bufB, gl, AB, CD);
+    if (active) {
+      constexpr int NA = ncart(LA), NB = ncart(LB);
+      for (int idx = gl; idx < NA * NB; idx += G) {
+        const int ib = idx % NB, ia = idx / NB;
+        const double v = res[idx] * c_cnorm[ncum(LA) + ia] * c_cnorm[ncum(LB) + ib];
+        const int mu = sa.fn + ia, nu = sb.fn + ib;
+        a.V[(int64_t)mu * a.nbf + nu] = v;
+        a.V[(int64_t)nu * a.nbf + mu] = v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int LA, int LB>
+static int launch_nuclear_cls(const OneArgs &a, cudaStream_t s) {
+  using O = Os<LA, LB, 0, 0>;
+  constexpr int G = O::G;
+  const int groups = 256 / G;
+  const size_t smem = (size_t)groups * O::SCR * 8;
+  auto kern = k_nuclear<LA, LB>;
+  BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int64_t blocks = (a.npair + groups - 1) / groups;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+// Overlap and kinetic energy by the 1-D Obara-Saika overlap recursion
+// S(i+1,j) = PA S(i,j) + (i S(i-1,j) + j S(i,j-1)) / (2p), and
+// T_x = [i j S(i-1,j-1) - 2b i S(i-1,j+1) - 2a j S(i+1,j-1) + 4ab S(i+1,j+1)] / 2
+// (the symmetric form of -1/2 d^2/dx^2).  One thread per shell pair.
+__global__ void k_overlap_kinetic(OneArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.npair) return;
+  const int2 pr = a.pairs[t];
+  const ShellRef sa = load_shell(a.orb, pr.x), sb = load_shell(a.orb, pr.y);
+  constexpr int LM = kMaxLOrb + 2;  // i, j up to l + 1
+  double Sv[36], Tv[36];
+  const int na = ncart(sa.l), nb = ncart(sb.l);
+  for (int k = 0; k < na * nb; ++k) Sv[k] = Tv[k] = 0.0;
+  for (int ia = 0; ia < sa.nprim; ++ia)
+    for (int ib = 0; ib < sb.nprim; ++ib) {
+      const double al = a.orb.exps[sa.poff + ia], be = a.orb.exps[sb.poff + ib];
+      const double p = al + be, ip = 1.0 / p;
+      double s1d[3][LM][LM];
+      double K = 1.0;
+      for (int x = 0; x < 3; ++x) {
+        const double P = (al * sa.xyz[x] + be * sb.xyz[x]) * ip;
+        const double PA = P - sa.xyz[x], PB = P - sb.xyz[x];
+        const double dAB = sa.xyz[x] - sb.xyz[x];
+        double (*S)[LM] = s1d[x];
+        S[0][0] = sqrt(3.141592653589793 * ip) * exp(-al * be * ip * dAB * dAB);
+        for (int j = 1; j < LM; ++j)
+          S[0][j] = PB * S[0][j - 1] + (j - 1) * 0.5 * ip * (j >= 2 ? S[0][j - 2] : 0.0);
+        for (int i = 1; i < LM; ++i)
+          for (int j = 0; j < LM; ++j) {
+            double v = PA * S[i - 1][j];
+            if (i >= 2) v += (i - 1) * 0.5 * ip * S[i - 2][j];
+            if (j >= 1) v += j * 0.5 * ip * S[i - 1][j - 1];
+            S[i][j] = v;
+          }
+        (void)K;
+      }
+      const double w = a.orb.coefs[sa.poff + ia] * a.orb.coefs[sb.poff + ib];
+      for (int ia2 = 0; ia2 < na; ++ia2) {
+        const unsigned char *ni = c_cart[ncum(sa.l) + ia2];
+        for (int ib2 = 0; ib2 < nb; ++ib2) {
+          const unsigned char *nj = c_cart[ncum(sb.l) + ib2];
+          double s[3], tk[3];
+          for (int x = 0; x < 3; ++x) {
+            const int i = ni[x], j = nj[x];
+            const double (*S)[LM] = s1d[x];
+            s[x] = S[i][j];
+            double v = 4.0 * al * be * S[i + 1][j + 1];
+            if (i >= 1) v -= 2.0 * be * i * S[i - 1][j + 1];
+            if (j >= 1) v -= 2.0 * al * j * S[i + 1][j - 1];
+            if (i >= 1 && j >= 1) v += i * j * S[i - 1][j - 1];
+            tk[x] = 0.5 * v;
+          }
+          Sv[ia2 * nb + ib2] += w * s[0] * s[1] * s[2];
+          Tv[ia2 * nb + ib2] += w * (tk[0] * s[1] * s[2] + s[0] * tk[1] * s[2] + s[0] * s[1] * tk[2]);
+        }
+      }
+    }
+  for (int ia2 = 0; ia2 < na; ++ia2)
+    for (int ib2 = 0; ib2 < nb; ++ib2) {
+      const double n = c_cnorm[ncum(sa.l) + ia2] * c_cnorm[ncum(sb.l) + ib2];
+      const int mu = sa.fn + ia2, nu = sb.fn + ib2;
+      if (a.S) {
+        a.S[(int64_t)mu * a.nbf + nu] = Sv[ia2 * nb + ib2] * n;
+        a.S[(int64_t)nu * a.nbf + mu] = Sv[ia2 * nb + ib2] * n;
+      }
+      if (a.T) {
+        a.T[(int64_t)mu * a.nbf + nu] = Tv[ia2 * nb + ib2] * n;
+        a.T[(int64_t)nu * a.nbf + mu] = Tv[ia2 * nb + ib2] * n;
+      }
+    }
+}
+
+int launch_one_electron(const Basis *b, double *S, double *T, double *V, cudaStream_t s) {
+  OneArgs a;
+  a.orb = b->orb.dev;
+  a.boys = b->ctx->boys;
+  a.atoms = b->d_atoms.as<double>();
+  a.natom = b->natom;
+  a.S = S;
+  a.T = T;
+  a.V = V;
+  a.nbf = b->nbf;
+  if (S || T) {
+    a.pairs = b->d_pairs.as<int2>();
+    a.npair = (int)b->npair_sh;
+    k_overlap_kinetic<<<(a.npair + 127) / 128, 128, 0, s>>>(a);
+    BQC_LAUNCH_CHECK();
+  }
+  if (V) {
+    for (int cls = 0; cls < kNPairClass; ++cls) {
+      const int np = b->pair_off[cls + 1] - b->pair_off[cls];
+      if (!np) continue;
+      a.pairs = b->d_pairs.as<int2>() + b->pair_off[cls];
+      a.npair = np;
+      int st = BQC_E_UNSUPPORTED;
+      switch (cls) {
+        case 0: st = launch_nuclear_cls<0, 0>(a, s); break;
+        case 1: st = launch_nuclear_cls<1, 0>(a, s); break;
+        case 2: st = launch_nuclear_cls<1, 1>(a, s); break;
+        case 3: st = launch_nuclear_cls<2, 0>(a, s); break;
+        case 4: st = launch_nuclear_cls<2, 1>(a, s); break;
+        case 5: st = launch_nuclear_cls<2, 2>(a, s); break;
+      }
+      BQC_TRY(st);
+    }
+  }
+  return BQC_OK;
+}
+
+// ------------------------------------------------------ screening plan ---
+
+__global__ void k_diag_sqrt_max(const double *V, int naux, const int *fn_of_shell,
+                                const int *l_of_shell, int nshell, double *q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nshell) return;
+  const int f0 = fn_of_shell[i], nc = ncart(l_of_shell[i]);
+  double m = 0.0;
+  for (int c = 0; c < nc; ++c) m = fmax(m, fabs(V[(int64_t)(f0 + c) * naux + f0 + c]));
+  q[i] = sqrt(m);
+}
+
+// cut[P] = number of class pairs with Q_pair * Q_P >= tau (pairs sorted descending).
+__global__ void k_cut(const double *qpair, int np, const int *aux_list, int na,
+                      const double *qaux, double tau, int64_t *cut) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= na) return;
+  const double qp = qaux[aux_list[i]];
+  int lo = 0, hi = np;  // first index with qpair*qp < tau
+  if (tau > 0.0) {
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (qpair[mid] * qp >= tau) lo = mid + 1; else hi = mid;
+    }
+  } else {
+    lo = np;
+  }
+  cut[i] = lo;
+}
+
+int eri3c_plan(const Basis *b, double tau, const double *V_diag_dev, cudaStream_t s,
+               Eri3cPlan *plan) {
+  Ctx *ctx = b->ctx;
+  plan->ctx = ctx;
+  plan->tau = tau;
+  const int64_t np = b->npair_sh;
+  const int nas = b->aux.dev.n;
+  BQC_TRY(plan->d_pairs_sorted.alloc(ctx, np * sizeof(int2)));
+  BQC_TRY(plan->d_qpair_sorted.alloc(ctx, np * sizeof(double)));
+  BQC_TRY(plan->d_qaux.alloc(ctx, nas * sizeof(double)));
+  DBuf qpair, keys_tmp;
+  BQC_TRY(qpair.alloc(ctx, np * sizeof(double)));
+  BQC_TRY(launch_schwarz_pairs(b, qpair.as<double>(), s));
+  k_diag_sqrt_max<<<(nas + 127) / 128, 128, 0, s>>>(V_diag_dev, b->naux, b->aux.dev.fn,
+                                                      b->aux.dev.l, nas, plan->d_qaux.as<double>());
+  BQC_LAUNCH_CHECK();
+  // sort each class segment by decreasing Q
+  for (int cls = 0; cls < kNPairClass; ++cls) {
+    const int o = b->pair_off[cls], n = b->pair_off[cls + 1] - o;
+    if (!n) continue;
+    size_t tmp = 0;
+    const double *kin = qpair.as<double>() + o;
+    double *kout = plan->d_qpair_sorted.as<double>() + o;
+    const int2 *vin = b->d_pairs.as<int2>() + o;
+    int2 *vout = plan->d_pairs_sorted.as<int2>() + o;
+    BQC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, kin, kout, vin, vout, n,
+                                                           0, 64, s));
+    DBuf t;
+    BQC_TRY(t.alloc(ctx, std::max<size_t>(tmp, 16)));
+    BQC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(t.p, tmp, kin, kout, vin, vout, n, 0,
+                                                           64, s));
+    BQC_CUDA_TRY(cudaStreamSynchronize(s));  // t is released at scope end
+  }
+  // survivor counts and prefixes per (class, aux l)
+  int64_t off = 0;
+  for (int cls = 0; cls < kNPairClass; ++cls)
+    for (int lc = 0; lc <= kMaxLAux; ++lc) {
+      plan->prefix_off[cls][lc] = off;
+      off += (b->auxl_off[lc + 1] - b->auxl_off[lc]) + 1;
+    }
+  BQC_TRY(plan->d_prefix.alloc(ctx, off * sizeof(int64_t)));
+  BQC_CUDA_TRY(cudaMemsetAsync(plan->d_prefix.p, 0, off * sizeof(int64_t), s));
+  DBuf cut;
+  BQC_TRY(cut.alloc(ctx, std::max<int64_t>(1, nas) * sizeof(int64_t)));
+  for (int cls = 0; cls < kNPairClass; ++cls) {
+    const int po = b->pair_off[cls], pn = b->pair_off[cls + 1] - po;
+    for (int lc = 0; lc <= kMaxLAux; ++lc) {
+      const int ao = b->auxl_off[lc], an = b->auxl_off[lc + 1] - ao;
+      if (!an) continue;
+      int64_t *pre = plan->d_prefix.as<int64_t>() + plan->prefix_off[cls][lc];
+      if (!pn) continue;
+      k_cut<<<(an + 127) / 128, 128, 0, s>>>(plan->d_qpair_sorted.as<double>() + po, pn,
+                                             b->d_aux_by_l.as<int>() + ao, an,
+                                             plan->d_qaux.as<double>(), tau, cut.as<int64_t>());
+      BQC_LAUNCH_CHECK();
+      size_t tmp = 0;
+      BQC_CUDA_TRY(cub::DeviceScan::InclusiveSum(nullptr, tmp, cut.as<int64_t>(), pre + 1, an, s));
+      DBuf t;
+      BQC_TRY(t.alloc(ctx, std::max<size_t>(tmp, 16)));
+      BQC_CUDA_TRY(cub::DeviceScan::InclusiveSum(t.p, tmp, cut.as<int64_t>(), pre + 1, an, s));
+      BQC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  // read the totals (one small copy)
+  std::vector<int64_t> h(off);
+  BQC_CUDA_TRY(cudaMemcpyAsync(h.data(), plan->d_prefix.p, off * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  plan->survivors = plan->candidates = 0;
+  for (int cls = 0; cls < kNPairClass; ++cls) {
+    const int pn = b->pair_off[cls + 1] - b->pair_off[cls];
+    for (int lc = 0; lc <= kMaxLAux; ++lc) {
+      const int an = b->auxl_off[lc + 1] - b->auxl_off[lc];
+      plan->total[cls][lc] = h[plan->prefix_off[cls][lc] + an];
+      plan->survivors += plan->total[cls][lc];
+      plan->candidates += (int64_t)an * pn;
+    }
+  }
+  return BQC_OK;
+}
+
+}  // namespace bqc

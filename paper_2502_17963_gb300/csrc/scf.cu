@@ -1,0 +1,369 @@
+// Closed-shell SCF driver around the DF Fock build (bqc_jk).
+//
+// Protocol (Szabo & Ostlund Sec. 3.4.6 with Pulay DIIS; identical to the
+// oracle's): canonical orthogonalisation X = U s^{-1/2} over eigenvalues of S
+// above orth_thresh; core-Hamiltonian guess; each iteration builds J, K from
+// C_occ, F = H + 2J - K, E = sum D (H + F) + E_nn, e = X^T (F D S - S D F) X;
+// converged when max|e| < diis_tol and |E - E_prev| < energy_tol; otherwise
+// DIIS over the last diis_space (F, e) pairs once two are stored, and
+// diagonalise X^T F X.  Precision staging: a MIXED first stage switches to
+// FP64 (DIIS history cleared) when max|e| < stage_tol, or when the mixed
+// stage stops improving (no new minimum of max|e| for 4 iterations), since
+// a TF32 Fock matrix carries errors near that size.
+//
+// Linear algebra here (eigh, small GEMMs, dots) uses cuSOLVER / cuBLAS in
+// FP64; everything is column-major; symmetric matrices need no conversion.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "bqc_internal.h"
+#include "df_internal.h"
+
+namespace bqc {
+
+#define BQC_BLAS_TRY(expr)                                                   \
+  do {                                                                       \
+    if ((expr) != CUBLAS_STATUS_SUCCESS) {                                   \
+      ::bqc::set_error("cuBLAS call failed: " #expr, __FILE__, __LINE__);    \
+      return BQC_E_CUDA;                                                     \
+    }                                                                        \
+  } while (0)
+#define BQC_SOLVER_TRY(expr)                                                 \
+  do {                                                                       \
+    if ((expr) != CUSOLVER_STATUS_SUCCESS) {                                 \
+      ::bqc::set_error("cuSOLVER call failed: " #expr, __FILE__, __LINE__);  \
+      return BQC_E_CUDA;                                                     \
+    }                                                                        \
+  } while (0)
+
+__global__ void k_axpby3(int64_t n, const double *a, double ca, const double *b, double cb,
+                         const double *c, double cc, double *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ca * a[i] + cb * b[i] + (c ? cc * c[i] : 0.0);
+}
+
+// out = M - M^T (column-major n x n)
+__global__ void k_antisym(int n, const double *M, double *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  const int64_t r = i % n, c = i / n;
+  out[i] = M[i] - M[r * n + c];
+}
+
+// X[:, j] = U[:, k0 + j] / sqrt(s[k0 + j])
+__global__ void k_orth(int n, int nmo, int k0, const double *U, const double *s, double *X) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * nmo) return;
+  const int64_t r = i % n, j = i / n;
+  X[i] = U[(k0 + j) * (int64_t)n + r] * rsqrt(s[k0 + j]);
+}
+
+// row-major out[r][c] = colmajor in[c * rows + r]  (rows x cols)
+__global__ void k_cm_to_rm(int rows, int cols, const double *in, int64_t ld, double *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows * cols) return;
+  const int64_t r = i / cols, c = i % cols;
+  out[i] = in[c * ld + r];
+}
+
+static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// Solves the (m+1) x (m+1) Pulay system by Gaussian elimination with partial
+// pivoting; returns false if singular.
+static bool diis_solve(const std::vector<double> &Bm, int m, std::vector<double> &c) {
+  const int n = m + 1;
+  std::vector<double> A((size_t)n * (n + 1), 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * (n + 1) + j] = Bm[(size_t)i * m + j];
+  for (int i = 0; i < m; ++i) {
+    A[(size_t)i * (n + 1) + m] = -1.0;
+    A[(size_t)m * (n + 1) + i] = -1.0;
+  }
+  A[(size_t)m * (n + 1) + n] = -1.0;  // rhs
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * (n + 1) + k]) > std::fabs(A[(size_t)p * (n + 1) + k])) p = i;
+    if (A[(size_t)p * (n + 1) + k] == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j <= n; ++j) std::swap(A[(size_t)p * (n + 1) + j], A[(size_t)k * (n + 1) + j]);
+    for (int i = k + 1; i < n; ++i) {
+      const double f = A[(size_t)i * (n + 1) + k] / A[(size_t)k * (n + 1) + k];
+      for (int j = k; j <= n; ++j) A[(size_t)i * (n + 1) + j] -= f * A[(size_t)k * (n + 1) + j];
+    }
+  }
+  std::vector<double> x(n);
+  for (int i = n - 1; i >= 0; --i) {
+    double v = A[(size_t)i * (n + 1) + n];
+    for (int j = i + 1; j < n; ++j) v -= A[(size_t)i * (n + 1) + j] * x[j];
+    x[i] = v / A[(size_t)i * (n + 1) + i];
+  }
+  c.assign(x.begin(), x.begin() + m);
+  for (double v : c)
+    if (!std::isfinite(v)) return false;
+  return true;
+}
+
+struct ScfWork {
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t sol = nullptr;
+  ~ScfWork() {
+    if (blas) cublasDestroy(blas);
+    if (sol) cusolverDnDestroy(sol);
+  }
+};
+
+// Symmetric eigen-decomposition in place (columns of A become eigenvectors).
+static int eigh(ScfWork &w, Ctx *ctx, double *A, int n, double *evals, DBuf &work, DBuf &info,
+                cudaStream_t s) {
+  int lwork = 0;
+  BQC_SOLVER_TRY(cusolverDnDsyevd_bufferSize(w.sol, CUSOLVER_EIG_MODE_VECTOR,
+                                             CUBLAS_FILL_MODE_LOWER, n, A, n, evals, &lwork));
+  if (work.n < (size_t)lwork * 8) BQC_TRY(work.alloc(ctx, (size_t)std::max(lwork, 1) * 8));
+  if (!info.p) BQC_TRY(info.alloc(ctx, sizeof(int)));
+  BQC_SOLVER_TRY(cusolverDnDsyevd(w.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A,
+                                  n, evals, work.as<double>(), lwork, info.as<int>()));
+  int h = 0;
+  BQC_CUDA_TRY(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h != 0) {
+    set_error("syevd did not converge", __FILE__, __LINE__);
+    return BQC_E_CUDA;
+  }
+  return BQC_OK;
+}
+
+int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_result *res) {
+  const Basis *b = df->basis;
+  const int n = b->nbf, no = b->nocc;
+  const int64_t nn = (int64_t)n * n;
+  ScfWork w;
+  BQC_BLAS_TRY(cublasCreate(&w.blas));
+  BQC_BLAS_TRY(cublasSetStream(w.blas, s));
+  BQC_BLAS_TRY(cublasSetPointerMode(w.blas, CUBLAS_POINTER_MODE_HOST));
+  BQC_BLAS_TRY(cublasSetMathMode(w.blas, CUBLAS_PEDANTIC_MATH));
+  BQC_SOLVER_TRY(cusolverDnCreate(&w.sol));
+  BQC_SOLVER_TRY(cusolverDnSetStream(w.sol, s));
+  DBuf S, T, V, H, F, J, K, D, X, U, ev, Cc, Fp, t1, t2, Crm, work, info, Fx;
+  for (DBuf *p : {&S, &T, &V, &H, &F, &J, &K, &D, &X, &U, &Cc, &Fp, &t1, &t2, &Fx})
+    BQC_TRY(p->alloc(ctx, nn * 8));
+  BQC_TRY(ev.alloc(ctx, (size_t)n * 8));
+  BQC_TRY(Crm.alloc(ctx, (size_t)n * no * 8));
+  BQC_TRY(launch_one_electron(b, S.as<double>(), T.as<double>(), V.as<double>(), s));
+  k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, T.as<double>(), 1.0, V.as<double>(), 1.0, nullptr, 0.0,
+                                    H.as<double>());
+  BQC_LAUNCH_CHECK();
+  // canonical orthogonalisation
+  BQC_CUDA_TRY(cudaMemcpyAsync(U.p, S.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+  BQC_TRY(eigh(w, ctx, U.as<double>(), n, ev.as<double>(), work, info, s));
+  std::vector<double> sv(n);
+  BQC_CUDA_TRY(cudaMemcpyAsync(sv.data(), ev.p, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  int k0 = 0;
+  while (k0 < n && !(sv[k0] > o.orth_thresh)) ++k0;
+  const int nmo = n - k0;
+  if (nmo < no) return BQC_E_INVALID;
+  k_orth<<<nblk((int64_t)n * nmo), 256, 0, s>>>(n, nmo, k0, U.as<double>(), ev.as<double>(),
+                                                X.as<double>());
+  BQC_LAUNCH_CHECK();
+  const double one = 1.0, zero = 0.0;
+  double *Xp = X.as<double>();
+  // diagonalise X^T M X -> C (n x nmo, column-major), eps
+  auto diag = [&](const double *M) -> int {
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nmo, n, &one, M, n, Xp, n,
+                             &zero, t1.as<double>(), n));
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_T, CUBLAS_OP_N, nmo, nmo, n, &one, Xp, n,
+                             t1.as<double>(), n, &zero, Fp.as<double>(), nmo));
+    BQC_TRY(eigh(w, ctx, Fp.as<double>(), nmo, ev.as<double>(), work, info, s));
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nmo, nmo, &one, Xp, n,
+                             Fp.as<double>(), nmo, &zero, Cc.as<double>(), n));
+    return BQC_OK;
+  };
+  BQC_TRY(diag(H.as<double>()));
+  const int space = std::max(1, o.diis_space);
+  std::vector<DBuf> hF(space), hE(space);
+  for (int i = 0; i < space; ++i) {
+    BQC_TRY(hF[i].alloc(ctx, nn * 8));
+    BQC_TRY(hE[i].alloc(ctx, (size_t)nmo * nmo * 8));
+  }
+  std::vector<int> slot;  // DIIS entries in age order (slot indices)
+  std::vector<double> Bm; // Gram matrix of errors in age order
+  int stage = o.prec;
+  int mixed_iters = 0, since_best = 0;
+  double best = INFINITY;
+  double E = 0.0, Eprev = 0.0, emax = INFINITY;
+  bool have_prev = false, converged = false;
+  int it = 0;
+  for (it = 1; it <= o.max_iter; ++it) {
+    k_cm_to_rm<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, Cc.as<double>(), n, Crm.as<double>());
+    BQC_LAUNCH_CHECK();
+    BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Crm.as<double>(), no, stage, J.as<double>(),
+                   K.as<double>(), (bqc_stream_t)s));
+    k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, J.as<double>(), 2.0,
+                                      K.as<double>(), -1.0, F.as<double>());
+    BQC_LAUNCH_CHECK();
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, no, &one, Cc.as<double>(), n,
+                             Cc.as<double>(), n, &zero, D.as<double>(), n));
+    k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, F.as<double>(), 1.0, nullptr, 0.0,
+                                      t2.as<double>());
+    BQC_LAUNCH_CHECK();
+    double eel = 0.0;
+    BQC_BLAS_TRY(cublasDdot(w.blas, (int)nn, D.as<double>(), 1, t2.as<double>(), 1, &eel));
+    E = eel + b->enuc;
+    // e = X^T (F D S - S D F) X
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, F.as<double>(), n,
+                             D.as<double>(), n, &zero, t1.as<double>(), n));
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, t1.as<double>(), n,
+                             S.as<double>(), n, &zero, t2.as<double>(), n));
+    k_antisym<<<nblk(nn), 256, 0, s>>>(n, t2.as<double>(), t1.as<double>());
+    BQC_LAUNCH_CHECK();
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nmo, n, &one, t1.as<double>(),
+                             n, Xp, n, &zero, t2.as<double>(), n));
+    // choose the DIIS slot for this iteration's error
+    int sl;
+    if ((int)slot.size() < space) {
+      std::vector<bool> used(space, false);
+      for (int q : slot) used[q] = true;
+      sl = 0;
+      while (used[sl]) ++sl;
+    } else {
+      sl = slot.front();
+    }
+    double *err = hE[sl].as<double>();
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_T, CUBLAS_OP_N, nmo, nmo, n, &one, Xp, n,
+                             t2.as<double>(), n, &zero, err, nmo));
+    int imax = 1;
+    BQC_BLAS_TRY(cublasIdamax(w.blas, nmo * nmo, err, 1, &imax));
+    double hv = 0.0;
+    BQC_CUDA_TRY(cudaMemcpyAsync(&hv, err + (imax - 1), 8, cudaMemcpyDeviceToHost, s));
+    BQC_CUDA_TRY(cudaStreamSynchronize(s));
+    emax = std::fabs(hv);
+    if (stage == BQC_PREC_FP64 && emax < o.diis_tol && have_prev &&
+        std::fabs(E - Eprev) < o.energy_tol) {
+      converged = true;
+      break;
+    }
+    if (stage != BQC_PREC_FP64) {
+      ++mixed_iters;
+      if (emax < best * 0.5) {
+        best = emax;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      if (emax < o.stage_tol || since_best >= 4) {
+        // switch to FP64: discard the mixed history, redo this iteration in FP64
+        stage = BQC_PREC_FP64;
+        slot.clear();
+        Bm.clear();
+        have_prev = false;
+        --it;
+        continue;
+      }
+    }
+    Eprev = E;
+    have_prev = true;
+    // DIIS bookkeeping
+    if ((int)slot.size() == space) {
+      // drop the oldest entry (row/col 0 of Bm)
+      const int m = (int)slot.size();
+      std::vector<double> nb((size_t)(m - 1) * (m - 1));
+      for (int i = 1; i < m; ++i)
+        for (int j = 1; j < m; ++j) nb[(size_t)(i - 1) * (m - 1) + j - 1] = Bm[(size_t)i * m + j];
+      Bm.swap(nb);
+      slot.erase(slot.begin());
+    }
+    BQC_CUDA_TRY(cudaMemcpyAsync(hF[sl].p, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+    {
+      const int m = (int)slot.size();
+      std::vector<double> nb((size_t)(m + 1) * (m + 1));
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) nb[(size_t)i * (m + 1) + j] = Bm[(size_t)i * m + j];
+      for (int i = 0; i <= m; ++i) {
+        const int si = (i < m) ? slot[i] : sl;
+        double d = 0.0;
+        BQC_BLAS_TRY(cublasDdot(w.blas, nmo * nmo, hE[si].as<double>(), 1, err, 1, &d));
+        nb[(size_t)i * (m + 1) + m] = d;
+        nb[(size_t)m * (m + 1) + i] = d;
+      }
+      Bm.swap(nb);
+      slot.push_back(sl);
+    }
+    const double *Fuse = F.as<double>();
+    const int m = (int)slot.size();
+    if (m >= 2) {
+      std::vector<double> c;
+      if (diis_solve(Bm, m, c)) {
+        BQC_CUDA_TRY(cudaMemsetAsync(Fx.p, 0, nn * 8, s));
+        for (int i = 0; i < m; ++i)
+          BQC_BLAS_TRY(cublasDaxpy(w.blas, (int)nn, &c[i], hF[slot[i]].as<double>(), 1,
+                                   Fx.as<double>(), 1));
+        Fuse = Fx.as<double>();
+      }
+    }
+    BQC_TRY(diag(Fuse));
+  }
+  if (it > o.max_iter) it = o.max_iter;
+  // results (library-owned buffers, row-major C)
+  res->energy = E;
+  res->e_nuc = b->enuc;
+  res->diis_err = emax;
+  res->iterations = it;
+  res->converged = converged ? 1 : 0;
+  res->iterations_mixed = mixed_iters;
+  res->nmo = nmo;
+  if (res->C_dev) {
+    k_cm_to_rm<<<nblk((int64_t)n * nmo), 256, 0, s>>>(n, nmo, Cc.as<double>(), n, res->C_dev);
+    BQC_LAUNCH_CHECK();
+  }
+  if (res->eps_dev)
+    BQC_CUDA_TRY(
+        cudaMemcpyAsync(res->eps_dev, ev.p, (size_t)nmo * 8, cudaMemcpyDeviceToDevice, s));
+  if (res->F_dev)
+    BQC_CUDA_TRY(cudaMemcpyAsync(res->F_dev, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  BQC_TRY(ctx->check_flag(s));
+  return converged ? BQC_OK : BQC_E_NOT_CONVERGED;
+}
+
+}  // namespace bqc
+
+using namespace bqc;
+
+extern "C" {
+
+int bqc_scf_run(bqc_ctx *ctx, bqc_df *df, const bqc_scf_opts *opts, bqc_stream_t stream,
+                bqc_scf_result *out) {
+  if (!ctx || !df || !out) return BQC_E_INVALID;
+  BQC_CUDA_TRY(cudaSetDevice(ctx->device));
+  bqc_scf_opts o;
+  o.diis_tol = 1e-8;
+  o.energy_tol = 1e-10;
+  o.stage_tol = 1e-5;
+  o.max_iter = 100;
+  o.diis_space = 8;
+  o.prec = BQC_PREC_FP64;
+  o.orth_thresh = 1e-8;
+  if (opts) {
+    o = *opts;
+    if (o.diis_tol <= 0) o.diis_tol = 1e-8;
+    if (o.energy_tol <= 0) o.energy_tol = 1e-10;
+    if (o.stage_tol <= 0) o.stage_tol = 1e-5;
+    if (o.max_iter <= 0) o.max_iter = 100;
+    if (o.diis_space <= 0) o.diis_space = 8;
+    if (o.orth_thresh <= 0) o.orth_thresh = 1e-8;
+  }
+  double *C = out->C_dev, *eps = out->eps_dev, *F = out->F_dev;
+  *out = bqc_scf_result{};
+  out->C_dev = C;
+  out->eps_dev = eps;
+  out->F_dev = F;
+  return scf_run(ctx, df, o, (cudaStream_t)stream, out);
+}
+
+}  // extern "C"

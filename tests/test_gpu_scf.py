@@ -1,0 +1,32 @@
+"""FP64 SCF energies on the GPU against the oracle (bar: 1e-8 Eh)."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bqc():
+    import paper_2502_17963_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("name", ["h2o", "w2", "w4"])
+def test_scf_energy_fp64(gpu_ctx, bqc, name):
+    mol = workload.molecule_for(name)
+    basis = bqc.Basis(gpu_ctx, mol)
+    df = bqc.DF(gpu_ctx, basis, keep_fp32=False)
+    r = bqc.scf_run(gpu_ctx, df, keep_arrays=True)
+    I = oracle.system_integrals(mol)
+    B, _ = oracle.df_tensor(I["aux"], I["orb"])
+    ro = oracle.rhf(I["S"], I["H"], lambda C: oracle.jk_df(B, C), mol.nocc, I["enuc"])
+    assert r["converged"] and ro.converged
+    assert abs(r["energy"] - ro.energy) < 1e-8, (r["energy"], ro.energy)
+    assert r["diis_err"] < 1e-8
+    # same density
+    C = r["C"].cpu().numpy()[:, : mol.nocc]
+    D = C @ C.T
+    assert np.abs(D - ro.D).max() < 1e-6
