@@ -56,10 +56,17 @@ enum {
   BQC_E_UNSUPPORTED = -9    /* angular momentum / size beyond this build    */
 };
 
-/* Precision of the Fock build (the K contraction and B.D products).
- * FP64: all FP64 (DFMA).  MIXED_TF32: B and C_occ shadows rounded to TF32,
- * tcgen05 kind::tf32 MMAs with FP32 accumulation, chunk sums in FP64. */
-typedef enum { BQC_PREC_FP64 = 0, BQC_PREC_MIXED_TF32 = 1 } bqc_prec;
+/* Precision of the Fock build (the X = B C and K contractions, the B.D
+ * products).  FP64: all FP64 (DFMA).  MIXED_TF32: tcgen05 kind::tf32 MMAs on
+ * TF32-rounded B and C_occ (one product per term, ~2^-11 relative per
+ * product), FP32 accumulation in short chains, FP64 chunk sums.
+ * MIXED_TF32X3: the same with every operand split hi + lo into two TF32
+ * parts and three products per term (hi*hi + hi*lo + lo*hi, ~2^-22). */
+typedef enum {
+  BQC_PREC_FP64 = 0,
+  BQC_PREC_MIXED_TF32 = 1,
+  BQC_PREC_MIXED_TF32X3 = 2
+} bqc_prec;
 
 typedef struct bqc_ctx bqc_ctx;
 typedef struct bqc_basis bqc_basis;
@@ -131,7 +138,8 @@ typedef struct {
   int mode;            /* bqc_df_mode                                         */
   double schwarz;      /* screening threshold; default 1e-12 stored, 1e-10 direct */
   int aux_block;       /* direct mode: aux functions per block (default 1024)  */
-  int keep_fp32;       /* stored mode: also keep the TF32-rounded full-square shadow */
+  int keep_fp32;       /* stored mode: also keep the split TF32 full-square shadows
+                          (needed by the mixed precisions)                     */
   size_t hbm_limit;    /* AUTO: choose DIRECT when STORED needs more (0 = free memory) */
 } bqc_df_opts;
 

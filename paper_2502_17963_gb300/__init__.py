@@ -24,6 +24,7 @@ BQC_E_NOT_CONVERGED = -4
 BQC_E_NOT_READY = -8
 PREC_FP64 = 0
 PREC_MIXED_TF32 = 1
+PREC_MIXED_TF32X3 = 2
 DF_STORED, DF_DIRECT, DF_AUTO = 0, 1, 2
 
 

@@ -73,41 +73,6 @@ __global__ void k_unpack_sym(const double *Jp, int n, double *J) {
   J[i] = Jp[hi * (hi + 1) / 2 + lo];
 }
 
-__device__ __forceinline__ float round_tf32(double x) {
-  // round to nearest TF32 (10 explicit mantissa bits), ties away from zero
-  uint32_t r;
-  const float f = (float)x;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-  return __uint_as_float(r);
-}
-
-// B32[P][mu][nu] = tf32(B64[P][tri(mu, nu)]) for the full square; rows
-// padded with zeros to ld columns (TMA strides must be multiples of 16 B).
-__global__ void k_expand_tf32(const double *__restrict__ B, int n, int ld, int64_t npair, int p0,
-                              int np, float *__restrict__ B32) {
-  const int64_t nn = (int64_t)n * ld;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nn * np) return;
-  const int64_t P = i / nn, rc = i % nn;
-  const int64_t r = rc / ld, c = rc % ld;
-  if (c >= n) {
-    B32[i] = 0.0f;
-    return;
-  }
-  const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
-  B32[i] = round_tf32(B[(p0 + P) * npair + hi * (hi + 1) / 2 + lo]);
-}
-
-int df_expand_tf32(const double *B64, int n, int64_t npair, int p0, int np, float *B32,
-                   cudaStream_t s) {
-  const int ld = mixed_ld(n);
-  const int64_t tot = (int64_t)n * ld * np;
-  if (!tot) return BQC_OK;
-  k_expand_tf32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B64, n, ld, npair, p0, np, B32);
-  BQC_LAUNCH_CHECK();
-  return BQC_OK;
-}
-
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux, no = b->nocc;
@@ -168,7 +133,7 @@ size_t df_stored_bytes(int n, int naux, int nocc, bool fp32) {
   b += (size_t)naux * n * nocc * 8;                                // X64
   b += npair * 8 + (size_t)naux * 8 * 2;
   if (fp32) {
-    b += (size_t)naux * n * mixed_ld(n) * 4;  // B32
+    b += (size_t)naux * n * mixed_ld(n) * 4;  // B32 (hi part)
     b += (size_t)naux * n * nocc * 4;       // X32
     b += (size_t)n * nocc * 4 * 2;          // C shadows
     b += mixed_workspace_bytes(n, naux, nocc);
@@ -250,9 +215,6 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
     if (o.keep_fp32) {
       if ((st = df->B32.alloc(ctx, (size_t)naux * n * mixed_ld(n) * 4)) != BQC_OK)
         return fail(st);
-      if ((st = df_expand_tf32(df->B64.as<double>(), n, npair, 0, naux, df->B32.as<float>(), s)) !=
-          BQC_OK)
-        return fail(st);
       if ((st = mixed_setup(df, s)) != BQC_OK) return fail(st);
     }
   } else {
@@ -327,9 +289,9 @@ int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K
   if (df->timing) df->timed = true;
   if (df->mode == BQC_DF_DIRECT) return jk_direct(df, C, prec, J, K, s);
   if (prec == BQC_PREC_FP64) return jk_fp64_stored(df, C, J, K, s);
-  if (prec == BQC_PREC_MIXED_TF32) {
+  if (prec == BQC_PREC_MIXED_TF32 || prec == BQC_PREC_MIXED_TF32X3) {
     if (!df->B32.p) return BQC_E_INVALID;
-    return jk_mixed_stored(df, C, J, K, s);
+    return jk_mixed_stored(df, C, prec, J, K, s);
   }
   return BQC_E_INVALID;
 }

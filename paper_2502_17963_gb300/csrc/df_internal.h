@@ -59,12 +59,10 @@ struct Df {
 size_t mixed_workspace_bytes(int n, int naux, int nocc);
 int mixed_ld(int n);  // row length of the TF32 shadow (N rounded up to 4)
 int mixed_setup(Df *df, cudaStream_t s);
-int jk_mixed_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
+int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 int direct_setup(Df *df, cudaStream_t s);
 int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
-int df_expand_tf32(const double *B64, int n, int64_t npair, int p0, int np, float *B32,
-                   cudaStream_t s);
 size_t df_stored_bytes(int n, int naux, int nocc, bool fp32);
 
 }  // namespace bqc

@@ -72,6 +72,9 @@ int make_tmap_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *
   return BQC_OK;
 }
 
+constexpr int kBM = 128;
+constexpr uint32_t kAStage = kBM * 128;  // 128 rows x 128 bytes
+
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
   const uint32_t a = smem_u32(p);
   return p + ((1024 - (a & 1023)) & 1023);
@@ -85,136 +88,207 @@ __device__ __forceinline__ float tf32r(float x) {
   return __uint_as_float(r);
 }
 
+// Precision design.
+//  * Split operands: an FP32 value f is held as hi = tf32(f), lo = tf32(f - hi)
+//    (hi + lo = f to ~2^-22).  SPLIT = 3 issues hi*hi + hi*lo + lo*hi per
+//    k-step ("3xTF32"), SPLIT = 1 only hi*hi (plain TF32, ~2^-11 per product).
+//  * Short accumulation chains: the tensor core adds into its FP32 TMEM
+//    accumulator with truncation, so a chain of S MMAs carries a relative bias
+//    growing with S (measured ~3e-5 after 390 steps).  Every chain here is one
+//    group of kGroupKb k-blocks; TMEM holds two accumulators, and while the
+//    MMA warp fills one, eight epilogue warps drain the other into register
+//    accumulators with round-to-nearest adds (X pass: FP32; SYRK:
+//    float-float, the compensation term kept in spare TMEM columns).
+
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, 8 epilogue warps
+constexpr int kGroupKb = 4;                    // k-blocks (of 32) per TMEM chain
+
 struct XpassParams {
-  int64_t rows;      // Naux * N
+  int64_t rows;      // Naux * N  (M of the GEMM)
   int n;             // N (rows per aux function)
-  int ldx;           // nocc_pad (row length of X32 and Cf)
-  int col0;          // first C column of this CTA's column group (blockIdx.y * cols)
-  int cols;          // columns per CTA (<= 512, multiple of 32)
-  int sub_n;         // columns per MMA (<= 256, multiple of 16)
-  int n_sub;         // MMAs per k-step
+  int ldx;           // row length of X and Cf
+  int ncg;           // column groups (tile columns = XN each)
   int kblocks;       // ceil(K / 32)
   int stages;
-  float *X;          // rows x ldx
+  int64_t tiles;     // row tiles x ncg
+  float *Xh, *Xl;    // rows x ldx (TF32 hi / lo parts)
   const float *Cf;   // N x ldx, fp32 C_occ
-  double *wrow;      // [ncg][rows]
-  int tmem_cols;     // power of two >= cols
+  float *wpart;      // [2 * ncg][rows] partial w per row
   int *flag;
 };
 
-constexpr int kBM = 128;
-constexpr uint32_t kAStage = kBM * 128;  // 128 rows x 128 bytes
-
-__global__ void __launch_bounds__(128, 1)
-    k_xpass_tf32(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+// Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
+// t / ncg, column group t % ncg), so neighbouring CTAs share A rows in L2.
+template <int XN, int SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_xpass_tf32(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+                 const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
                  const XpassParams p) {
+  constexpr int HALF = XN / 2;
+  constexpr int NS = SPLIT == 3 ? 2 : 1;  // operand parts per side
+  constexpr uint32_t a_bytes = kAStage, c_bytes = XN * 128;
+  constexpr uint32_t stage_bytes = NS * (a_bytes + c_bytes);
+  constexpr int TCOLS = (2 * XN <= 32) ? 32 : (2 * XN <= 64) ? 64 : (2 * XN <= 128) ? 128
+                                            : (2 * XN <= 256) ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  const uint32_t bstage = (uint32_t)p.cols * 128;
-  const uint32_t stage_bytes = kAStage + bstage;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages,
-                 done = full0 + 16 * p.stages;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
+  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    prefetch_tmap(&mapA);
-    prefetch_tmap(&mapB);
+    prefetch_tmap(&mapAh);
+    prefetch_tmap(&mapCh);
+    if (SPLIT == 3) {
+      prefetch_tmap(&mapAl);
+      prefetch_tmap(&mapCl);
+    }
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
     fence_barrier_init();
   }
-  if (warp == 0) tmem_alloc(smem_u32(tslot), p.tmem_cols);
+  if (warp == 0) tmem_alloc(smem_u32(tslot), TCOLS);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM;
-  const int cg = blockIdx.y;
   const uint32_t sbase = smem_u32(smem);
+  const int ngroups = (p.kblocks + kGroupKb - 1) / kGroupKb;
   bool ok = true;
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-      const int s = kb % p.stages;
-      if (kb >= p.stages) ok = mbar_wait(empty0 + 8 * s, ((kb / p.stages) - 1) & 1, p.flag, 11);
-      if (!ok) break;
-      const uint32_t a = sbase + s * stage_bytes, b = a + kAStage;
-      mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
-      tma_load_2d(a, &mapA, full0 + 8 * s, kb * 32, (int)m0);
-      for (int j = 0; j < p.n_sub; ++j)
-        tma_load_2d(b + j * p.sub_n * 128, &mapB, full0 + 8 * s, kb * 32,
-                    p.col0 + cg * p.cols + j * p.sub_n);
-    }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_tf32(kBM, p.sub_n);
-    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-      const int s = kb % p.stages;
-      ok = mbar_wait(full0 + 8 * s, (kb / p.stages) & 1, p.flag, 12);
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t a = sbase + s * stage_bytes, b = a + kAStage;
-#pragma unroll
-      for (int k4 = 0; k4 < 4; ++k4) {
-        const uint64_t ad = sdesc_sw128(a + k4 * 32);
-        for (int j = 0; j < p.n_sub; ++j) {
-          const uint64_t bd = sdesc_sw128(b + j * p.sub_n * 128 + k4 * 32);
-          mma_tf32(tbase + j * p.sub_n, ad, bd, idesc, (kb | k4) != 0);
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t kg = 0;  // k-blocks issued by this CTA
+      for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
+        const int64_t m0 = (t / p.ncg) * kBM;
+        const int c0 = (int)(t % p.ncg) * XN;
+        for (int kb = 0; kb < p.kblocks && ok; ++kb, ++kg) {
+          const int s = (int)(kg % p.stages);
+          if (kg >= p.stages)
+            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 11);
+          if (!ok) break;
+          const uint32_t a = sbase + s * stage_bytes;  // [Ah][Al][Ch][Cl]
+          const uint32_t bar = full0 + 8 * s;
+          mbar_arrive_expect_tx(bar, stage_bytes);
+          tma_load_2d(a, &mapAh, bar, kb * 32, (int)m0);
+          if (SPLIT == 3) tma_load_2d(a + a_bytes, &mapAl, bar, kb * 32, (int)m0);
+          tma_load_2d(a + NS * a_bytes, &mapCh, bar, kb * 32, c0);
+          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, &mapCl, bar, kb * 32, c0);
         }
       }
-      mma_commit(empty0 + 8 * s);
     }
-    mma_commit(done);
-  }
-  __syncwarp();
-  // epilogue: thread = accumulator row
-  ok = mbar_wait(done, 0, p.flag, 13);
-  __syncwarp();
-  tc_fence_after();
-  const int64_t row = m0 + warp * 32 + lane;
-  const bool valid = ok && row < p.rows;
-  const int mu = (int)(row % p.n);
-  double wsum = 0.0;
-  float wpart = 0.0f;
-  const int cbase = cg * p.cols;
-  for (int c = 0; c < p.n_sub * p.sub_n; c += 16) {
-    float v[16];
-    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c, v);
-    if (valid) {
-      float *xr = p.X + row * p.ldx + cbase + c;
-      const float *cr = p.Cf + (int64_t)mu * p.ldx + cbase + c;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kBM, XN);
+      int64_t kg = 0, g = 0;
+      for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
+        for (int gr = 0; gr < ngroups && ok; ++gr, ++g) {
+          const int b = (int)(g & 1);
+          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 14);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tbase + b * XN;
+          const int kb0 = gr * kGroupKb, kb1 = min(p.kblocks, kb0 + kGroupKb);
+          for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
+            const int s = (int)(kg % p.stages);
+            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / p.stages) & 1), p.flag, 12);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = sbase + s * stage_bytes, al = ah + a_bytes;
+            const uint32_t ch = ah + NS * a_bytes, cl = ch + c_bytes;
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        // stored TF32-rounded (round to nearest): the SYRK operand is exact TF32
-        *reinterpret_cast<float4 *>(xr + q) =
-            make_float4(tf32r(v[q]), tf32r(v[q + 1]), tf32r(v[q + 2]), tf32r(v[q + 3]));
-        const float4 cc = *reinterpret_cast<const float4 *>(cr + q);
-        wpart = fmaf(v[q], cc.x, wpart);
-        wpart = fmaf(v[q + 1], cc.y, wpart);
-        wpart = fmaf(v[q + 2], cc.z, wpart);
-        wpart = fmaf(v[q + 3], cc.w, wpart);
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t first = ((kb - kb0) | k4) != 0;
+              mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, first);
+              if (SPLIT == 3) {
+                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(cl + k4 * 32), idesc, 1);
+                mma_tf32(d, sdesc_sw128(al + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, 1);
+              }
+            }
+            mma_commit(empty0 + 8 * s);
+          }
+          mma_commit(tfull0 + 8 * b);
+        }
       }
     }
-    if ((c & 127) == 112) {  // fold every 128 columns into FP64
-      wsum += wpart;
-      wpart = 0.0f;
+  } else {
+    // epilogue warps: quadrant q of TMEM lanes, column half h
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    int64_t g = 0;
+    for (int64_t t = blockIdx.x; t < p.tiles; t += gridDim.x) {
+      const int64_t m0 = (t / p.ncg) * kBM;
+      const int cg = (int)(t % p.ncg);
+      float acc[HALF];
+#pragma unroll
+      for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
+      for (int gr = 0; gr < ngroups; ++gr, ++g) {
+        const int b = (int)(g & 1);
+        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 13);
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * XN + h * HALF;
+#pragma unroll
+        for (int c = 0; c < HALF; c += 16) {
+          float v[16];
+          tmem_ld16(ta + c, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      }
+      const int64_t row = m0 + q * 32 + lane;
+      if (ok && row < p.rows) {
+        const int mu = (int)(row % p.n);
+        const int col = cg * XN + h * HALF;
+        float *xh = p.Xh + row * p.ldx + col;
+        float *xl = p.Xl + row * p.ldx + col;
+        const float *cr = p.Cf + (int64_t)mu * p.ldx + col;
+        float wsum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < HALF; c += 4) {
+          const float4 cc = *reinterpret_cast<const float4 *>(cr + c);
+          wsum = fmaf(acc[c], cc.x, wsum);
+          wsum = fmaf(acc[c + 1], cc.y, wsum);
+          wsum = fmaf(acc[c + 2], cc.z, wsum);
+          wsum = fmaf(acc[c + 3], cc.w, wsum);
+          float4 hv, lv;
+          hv.x = tf32r(acc[c]);
+          hv.y = tf32r(acc[c + 1]);
+          hv.z = tf32r(acc[c + 2]);
+          hv.w = tf32r(acc[c + 3]);
+          *reinterpret_cast<float4 *>(xh + c) = hv;
+          if (SPLIT == 3) {
+            lv.x = tf32r(acc[c] - hv.x);
+            lv.y = tf32r(acc[c + 1] - hv.y);
+            lv.z = tf32r(acc[c + 2] - hv.z);
+            lv.w = tf32r(acc[c + 3] - hv.w);
+            *reinterpret_cast<float4 *>(xl + c) = lv;
+          }
+        }
+        p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum;
+      }
     }
   }
-  wsum += wpart;
-  if (valid) p.wrow[(int64_t)cg * p.rows + row] = wsum;
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, p.tmem_cols);
+  if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
 
-// w[P] = sum_cg sum_mu wrow[cg][P*N + mu]; also the fp32 copy for the J pass.
-__global__ void __launch_bounds__(256) k_wreduce(const double *wrow, int64_t rows, int ncg, int n,
-                                                 double *w, float *w32) {
+// w[P] = sum over partials and mu of wpart[k][P*N + mu] (FP64); also fp32 w.
+__global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t rows, int nparts,
+                                                 int n, double *w, float *w32) {
   const int P = blockIdx.x;
   double s = 0.0;
-  for (int g = 0; g < ncg; ++g)
-    for (int m = threadIdx.x; m < n; m += blockDim.x) s += wrow[g * rows + (int64_t)P * n + m];
+  for (int g = 0; g < nparts; ++g)
+    for (int m = threadIdx.x; m < n; m += blockDim.x) s += wpart[g * rows + (int64_t)P * n + m];
   __shared__ double red[256];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -232,103 +306,195 @@ __global__ void __launch_bounds__(256) k_wreduce(const double *wrow, int64_t row
 
 struct SyrkParams {
   int n, ldx, naux;
-  int ntile, ntri;
-  int p_per_chunk;
-  int nib;     // ldx / 32
+  int ntri;
+  int nchunk, p_per_chunk;
+  int nib;       // ldx / 32
   int stages;
-  float *part; // [chunk][ntri][128][128]
+  double *part;  // [chunk][ntri][128][128]
   int *flag;
 };
 
-__global__ void __launch_bounds__(128, 1)
-    k_syrk_tf32(const __grid_constant__ CUtensorMap mapX, const SyrkParams p) {
+__device__ __forceinline__ void tile_of(int t, int &tm, int &tn) {
+  int m = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((m + 1) * (m + 2) / 2 <= t) ++m;
+  while (m * (m + 1) / 2 > t) --m;
+  tm = m;
+  tn = t - m * (m + 1) / 2;
+}
+
+constexpr int kSyCols = kBM / (kEpiWarps / 4);  // columns per epilogue thread
+constexpr uint32_t kLoCol = 2 * kBM;             // TMEM columns of the compensation term
+
+// Persistent SYRK over work items (lower tile, aux chunk); item i -> tile
+// i % ntri, chunk i / ntri.  Partial tiles are written in FP64.
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_syrk_tf32(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
+                const SyrkParams p) {
+  constexpr int NS = SPLIT == 3 ? 2 : 1;
+  constexpr uint32_t stage_bytes = NS * 2 * kAStage;  // [Xh(tm)][Xh(tn)][Xl(tm)][Xl(tn)]
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  constexpr uint32_t stage_bytes = 2 * kAStage;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages,
-                 done = full0 + 16 * p.stages;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
+  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x, chunk = blockIdx.y;
-  int tm = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-  while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
-  while (tm * (tm + 1) / 2 > t) --tm;
-  const int tn = t - tm * (tm + 1) / 2;
-  const int P0 = chunk * p.p_per_chunk;
-  const int P1 = min(p.naux, P0 + p.p_per_chunk);
-  const int kblocks = max(0, P1 - P0) * p.nib;
+  const int items = p.ntri * p.nchunk;
   if (threadIdx.x == 0) {
-    prefetch_tmap(&mapX);
+    prefetch_tmap(&mapXh);
+    if (SPLIT == 3) prefetch_tmap(&mapXl);
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
     fence_barrier_init();
   }
-  if (warp == 0) tmem_alloc(smem_u32(tslot), 128);
+  if (warp == 0) tmem_alloc(smem_u32(tslot), 512);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t sbase = smem_u32(smem);
   bool ok = true;
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
-      const int s = kb % p.stages;
-      if (kb >= p.stages) ok = mbar_wait(empty0 + 8 * s, ((kb / p.stages) - 1) & 1, p.flag, 21);
-      if (!ok) break;
-      const int P = P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
-      const uint32_t a = sbase + s * stage_bytes, b = a + kAStage;
-      mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
-      tma_load_3d(a, &mapX, full0 + 8 * s, i0, tm * kBM, P);
-      tma_load_3d(b, &mapX, full0 + 8 * s, i0, tn * kBM, P);
+  auto chunk_kb = [&](int ch, int &P0, int &nkb) {
+    P0 = ch * p.p_per_chunk;
+    nkb = max(0, min(p.naux, P0 + p.p_per_chunk) - P0) * p.nib;
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t kg = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int tm, tn, P0, nkb;
+        tile_of(it % p.ntri, tm, tn);
+        chunk_kb(it / p.ntri, P0, nkb);
+        for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
+          const int s = (int)(kg % p.stages);
+          if (kg >= p.stages)
+            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 21);
+          if (!ok) break;
+          const int P = P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
+          const uint32_t a = sbase + s * stage_bytes, bar = full0 + 8 * s;
+          mbar_arrive_expect_tx(bar, stage_bytes);
+          tma_load_3d(a, &mapXh, bar, i0, tm * kBM, P);
+          tma_load_3d(a + kAStage, &mapXh, bar, i0, tn * kBM, P);
+          if (SPLIT == 3) {
+            tma_load_3d(a + 2 * kAStage, &mapXl, bar, i0, tm * kBM, P);
+            tma_load_3d(a + 3 * kAStage, &mapXl, bar, i0, tn * kBM, P);
+          }
+        }
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_tf32(kBM, kBM);
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
-      const int s = kb % p.stages;
-      ok = mbar_wait(full0 + 8 * s, (kb / p.stages) & 1, p.flag, 22);
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t a = sbase + s * stage_bytes, b = a + kAStage;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kBM, kBM);
+      int64_t kg = 0, g = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int P0, nkb;
+        chunk_kb(it / p.ntri, P0, nkb);
+        for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKb, ++g) {
+          const int b = (int)(g & 1);
+          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 24);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tbase + b * kBM;
+          const int kb1 = min(nkb, kb0 + kGroupKb);
+          for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
+            const int s = (int)(kg % p.stages);
+            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / p.stages) & 1), p.flag, 22);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t hm = sbase + s * stage_bytes, hn = hm + kAStage;
+            const uint32_t lm = hm + 2 * kAStage, ln = hm + 3 * kAStage;
 #pragma unroll
-      for (int k4 = 0; k4 < 4; ++k4)
-        mma_tf32(tbase, sdesc_sw128(a + k4 * 32), sdesc_sw128(b + k4 * 32), idesc,
-                 (kb | k4) != 0);
-      mma_commit(empty0 + 8 * s);
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t first = ((kb - kb0) | k4) != 0;
+              mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, first);
+              if (SPLIT == 3) {
+                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(ln + k4 * 32), idesc, 1);
+                mma_tf32(d, sdesc_sw128(lm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, 1);
+              }
+            }
+            mma_commit(empty0 + 8 * s);
+          }
+          mma_commit(tfull0 + 8 * b);
+        }
+      }
     }
-    mma_commit(done);
-  }
-  __syncwarp();
-  if (kblocks > 0) ok = mbar_wait(done, 0, p.flag, 23);
-  __syncwarp();
-  tc_fence_after();
-  const int r = warp * 32 + lane;
-  float *dst = p.part + (((int64_t)chunk * p.ntri + t) * kBM + r) * kBM;
-  for (int c = 0; c < kBM; c += 16) {
-    float v[16];
-    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c, v);
-    if (kblocks == 0 || !ok) {
+  } else {
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int64_t g = 0;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      int P0, nkb;
+      chunk_kb(it / p.ntri, P0, nkb);
+      float hi[kSyCols];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+      for (int c = 0; c < kSyCols; ++c) hi[c] = 0.0f;
+      {  // zero the compensation columns
+        float z[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kSyCols; c += 16) tmem_st16(tbase + lane_base + kLoCol + h * kSyCols + c, z);
+      }
+      for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKb, ++g) {
+        const int b = (int)(g & 1);
+        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 23);
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t ta = tbase + lane_base + b * kBM + h * kSyCols;
+        const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+#pragma unroll
+        for (int c = 0; c < kSyCols; c += 16) {
+          float v[16], lo[16];
+          tmem_ld16(ta + c, v);
+          tmem_ld16(tl + c, lo);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {  // two-sum: (hi, lo) += v
+            const float s = hi[c + i] + v[i];
+            const float bp = s - hi[c + i];
+            lo[i] += (hi[c + i] - (s - bp)) + (v[i] - bp);
+            hi[c + i] = s;
+          }
+          tmem_st16(tl + c, lo);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      }
+      const int r = q * 32 + lane;
+      double *dst =
+          p.part + (((int64_t)(it / p.ntri) * p.ntri + it % p.ntri) * kBM + r) * kBM + h * kSyCols;
+      const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+#pragma unroll
+      for (int c = 0; c < kSyCols; c += 16) {
+        float lo[16];
+        tmem_ld16(tl + c, lo);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+          const double2 v = make_double2(ok ? (double)hi[c + i] + (double)lo[i] : 0.0,
+                                         ok ? (double)hi[c + i + 1] + (double)lo[i + 1] : 0.0);
+          *reinterpret_cast<double2 *>(dst + c + i) = v;
+        }
+      }
     }
-#pragma unroll
-    for (int q = 0; q < 16; q += 4)
-      *reinterpret_cast<float4 *>(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
-// K = sum over chunks of the partial tiles, in FP64, symmetric.  One block
-// per (lower tile, 32-row strip): sums into shared memory, writes the strip
-// and its mirror image coalesced.
-__global__ void __launch_bounds__(256) k_syrk_reduce(const float *part, int nchunk, int ntri,
+// K = sum over chunks of the FP64 partial tiles, symmetric.  One block per
+// (lower tile, 32-row strip): sums into shared memory, writes the strip and
+// its mirror image coalesced.
+__global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nchunk, int ntri,
                                                      int n, double *K) {
   __shared__ double strip[32][kBM + 1];
-  const int t = blockIdx.x, sr = blockIdx.y;  // strip of 32 rows
+  const int t = blockIdx.x, sr = blockIdx.y;
   int tm = 0;
   while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
   const int tn = t - tm * (tm + 1) / 2;
@@ -336,8 +502,7 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const float *part, int nchu
     const int rr = e / kBM, c = e % kBM;
     const int r = sr * 32 + rr;
     double s = 0.0;
-    for (int ch = 0; ch < nchunk; ++ch)
-      s += part[(((int64_t)ch * ntri + t) * kBM + r) * kBM + c];
+    for (int ch = 0; ch < nchunk; ++ch) s += part[(((int64_t)ch * ntri + t) * kBM + r) * kBM + c];
     strip[rr][c] = s;
   }
   __syncthreads();
@@ -346,7 +511,6 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const float *part, int nchu
     const int mu = tm * kBM + sr * 32 + rr, nu = tn * kBM + c;
     if (mu < n && nu < n && (tm != tn || nu <= mu)) K[(int64_t)mu * n + nu] = strip[rr][c];
   }
-  // mirror: K[nu][mu] for nu in the tn tile, mu in this strip
   for (int e = threadIdx.x; e < 32 * kBM; e += blockDim.x) {
     const int c = e / 32, rr = e % 32;
     const int mu = tm * kBM + sr * 32 + rr, nu = tn * kBM + c;
@@ -356,11 +520,13 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const float *part, int nchu
 
 // -------------------------------------------------------------- J pass ---
 
-// J[mu][nu <= mu] = sum_P w_P B32[P][mu][nu] into packed FP64.  Block b owns
-// rows b and N-1-b (balanced work); a thread owns 4 consecutive columns of
-// one row and streams every P (float4 loads, FP32 partial sums over 64 P,
-// folded into FP64).
-__global__ void __launch_bounds__(512) k_jpass_tf32(const float *__restrict__ B32,
+// J[mu][nu <= mu] = sum_P w_P B[P][mu][nu] into packed FP64, B = Bh (+ Bl).
+// Block b owns rows b and N-1-b (balanced work); a thread owns 4 consecutive
+// columns of one row and streams every P (float4 loads, FP32 partial sums
+// over 64 P, folded into FP64).
+template <int SPLIT>
+__global__ void __launch_bounds__(512) k_jpass_tf32(const float *__restrict__ Bh,
+                                                    const float *__restrict__ Bl,
                                                     const float *__restrict__ w32, int naux, int n,
                                                     int ld, double *__restrict__ Jp) {
   const int b = blockIdx.x;
@@ -369,32 +535,39 @@ __global__ void __launch_bounds__(512) k_jpass_tf32(const float *__restrict__ B3
   const int c2 = (r2 != r1) ? r2 / 4 + 1 : 0;
   const int64_t nn = (int64_t)n * ld;
   for (int it = threadIdx.x; it < c1 + c2; it += blockDim.x) {
-  const int row = it < c1 ? r1 : r2;
-  const int q = it < c1 ? it : it - c1;
-  const float *src = B32 + (int64_t)row * ld + 4 * q;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int P0 = 0; P0 < naux; P0 += 64) {
-    const int P1 = min(naux, P0 + 64);
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int row = it < c1 ? r1 : r2;
+    const int q = it < c1 ? it : it - c1;
+    const int64_t off = (int64_t)row * ld + 4 * q;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int P0 = 0; P0 < naux; P0 += 64) {
+      const int P1 = min(naux, P0 + 64);
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
-    for (int P = P0; P < P1; ++P) {
-      const float4 v = __ldg(reinterpret_cast<const float4 *>(src + P * nn));
-      const float wp = __ldg(w32 + P);
-      a.x = fmaf(wp, v.x, a.x);
-      a.y = fmaf(wp, v.y, a.y);
-      a.z = fmaf(wp, v.z, a.z);
-      a.w = fmaf(wp, v.w, a.w);
+      for (int P = P0; P < P1; ++P) {
+        const float wp = __ldg(w32 + P);
+        float4 v = __ldg(reinterpret_cast<const float4 *>(Bh + off + P * nn));
+        if (SPLIT == 3) {
+          const float4 l = __ldg(reinterpret_cast<const float4 *>(Bl + off + P * nn));
+          v.x += l.x;
+          v.y += l.y;
+          v.z += l.z;
+          v.w += l.w;
+        }
+        a.x = fmaf(wp, v.x, a.x);
+        a.y = fmaf(wp, v.y, a.y);
+        a.z = fmaf(wp, v.z, a.z);
+        a.w = fmaf(wp, v.w, a.w);
+      }
+      acc[0] += a.x;
+      acc[1] += a.y;
+      acc[2] += a.z;
+      acc[3] += a.w;
     }
-    acc[0] += a.x;
-    acc[1] += a.y;
-    acc[2] += a.z;
-    acc[3] += a.w;
-  }
-  const int64_t base = (int64_t)row * (row + 1) / 2;
-  for (int k = 0; k < 4; ++k) {
-    const int col = 4 * q + k;
-    if (col <= row) Jp[base + col] = acc[k];
-  }
+    const int64_t base = (int64_t)row * (row + 1) / 2;
+    for (int k = 0; k < 4; ++k) {
+      const int col = 4 * q + k;
+      if (col <= row) Jp[base + col] = acc[k];
+    }
   }
 }
 
@@ -406,20 +579,22 @@ __global__ void k_unpack_sym2(const double *Jp, int n, double *J) {
   J[i] = Jp[hi * (hi + 1) / 2 + lo];
 }
 
-// Ct[i][nu] = tf32(C[nu][i]) (zero padded to ldx x ld), Cf[mu][i] = fp32 C.
-__global__ void k_prep_c(const double *C, int n, int nocc, int ld, int ldx, float *Ct,
+// Split of C_occ: Ch[i][nu] = tf32(c), Cl[i][nu] = tf32(c - Ch) with c = fp32(C[nu][i])
+// (zero padded to ldx x ld), and Cf[mu][i] = fp32 C.
+__global__ void k_prep_c(const double *C, int n, int nocc, int ld, int ldx, float *Ch, float *Cl,
                          float *Cf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t tot = (int64_t)ldx * ld;
   if (i < tot) {
     const int oi = (int)(i / ld), nu = (int)(i % ld);
-    float v = 0.0f;
+    float h = 0.0f, l = 0.0f;
     if (oi < nocc && nu < n) {
-      uint32_t r;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)C[(int64_t)nu * nocc + oi]));
-      v = __uint_as_float(r);
+      const float f = (float)C[(int64_t)nu * nocc + oi];
+      h = tf32r(f);
+      l = tf32r(f - h);
     }
-    Ct[i] = v;
+    Ch[i] = h;
+    if (Cl) Cl[i] = l;
   }
   if (i < (int64_t)n * ldx) {
     const int mu = (int)(i / ldx), oi = (int)(i % ldx);
@@ -427,112 +602,187 @@ __global__ void k_prep_c(const double *C, int n, int nocc, int ld, int ldx, floa
   }
 }
 
+// B (FP64 packed lower triangle) -> full-square split shadows Bh, Bl
+// ([P][mu][ld], rows zero-padded to ld columns: TMA strides are multiples of 16 B).
+__global__ void k_expand_split(const double *__restrict__ B, int n, int ld, int64_t npair, int p0,
+                               int np, float *__restrict__ Bh, float *__restrict__ Bl) {
+  const int64_t nn = (int64_t)n * ld;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn * np) return;
+  const int64_t P = i / nn, rc = i % nn;
+  const int64_t r = rc / ld, c = rc % ld;
+  float h = 0.0f, l = 0.0f;
+  if (c < n) {
+    const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
+    const float f = (float)B[(p0 + P) * npair + hi * (hi + 1) / 2 + lo];
+    h = tf32r(f);
+    l = tf32r(f - h);
+  }
+  Bh[i] = h;
+  if (Bl) Bl[i] = l;
+}
+
 // ------------------------------------------------------------- driver ----
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct MixedPlan {
-  int ld;        // B32 row length (N rounded to 4)
-  int ldx;       // nocc rounded to 32
-  int ncg;       // column groups of the X pass
-  int cols;      // columns per group
-  int sub_n, n_sub;
-  int xp_stages;
-  size_t xp_smem;
+  int ld;        // B shadow row length (N rounded to 4)
+  int ldx;       // X row length = ncg * xn
+  int ncg, xn;   // X-pass column groups and tile width
+  int xp_stages[2];   // [split1, split3]
+  size_t xp_smem[2];
   int ntile, ntri, nchunk, ppc;
-  int sy_stages;
-  size_t sy_smem;
+  int sy_stages[2];
+  size_t sy_smem[2];
+  int grid;      // persistent grid size (SM count)
 };
 
-static MixedPlan mixed_plan(int n, int naux, int nocc) {
+static MixedPlan mixed_plan(int n, int naux, int nocc, int nsm) {
   MixedPlan m;
+  m.grid = nsm;
   m.ld = round_up(n, 4);
   const int ldx0 = round_up(std::max(nocc, 1), 32);
-  m.ncg = (ldx0 + 511) / 512;
-  m.cols = round_up((ldx0 + m.ncg - 1) / m.ncg, 32);
-  m.ldx = m.ncg * m.cols;  // every column group is full
-  m.n_sub = (m.cols + 255) / 256;
-  m.sub_n = m.cols / m.n_sub;  // multiple of 16 since cols is a multiple of 32
-  const size_t stage = kAStage + (size_t)m.cols * 128;
+  m.ncg = (ldx0 + 255) / 256;
+  m.xn = round_up((ldx0 + m.ncg - 1) / m.ncg, 32);
+  m.ldx = m.ncg * m.xn;
   const size_t avail = 232448 - 1024 - 256;
-  m.xp_stages = (int)std::min<size_t>(4, avail / stage);
-  m.xp_smem = m.xp_stages * stage + 1024 + 256;
+  for (int k = 0; k < 2; ++k) {
+    const size_t stage = (size_t)(k + 1) * (kAStage + (size_t)m.xn * 128);
+    m.xp_stages[k] = (int)std::min<size_t>(8, avail / stage);
+    m.xp_smem[k] = m.xp_stages[k] * stage + 1024 + 256;
+    const size_t sst = (size_t)(k + 1) * 2 * kAStage;
+    m.sy_stages[k] = (int)std::min<size_t>(8, avail / sst);
+    m.sy_smem[k] = m.sy_stages[k] * sst + 1024 + 256;
+  }
   m.ntile = (n + kBM - 1) / kBM;
   m.ntri = m.ntile * (m.ntile + 1) / 2;
-  m.nchunk = std::max(1, std::min(naux, (2 * 152 + m.ntri - 1) / m.ntri));
-  m.ppc = (naux + m.nchunk - 1) / m.nchunk;
+  // work items about two per SM, chunks of at least 16 aux functions
+  int nchunk = std::max(1, (nsm + m.ntri - 1) / m.ntri);
+  while (nchunk * m.ntri < 2 * nsm && nchunk * 16 < naux) ++nchunk;
+  nchunk = std::min(nchunk, std::max(1, naux));
+  m.ppc = (naux + nchunk - 1) / nchunk;
   m.nchunk = (naux + m.ppc - 1) / m.ppc;
-  m.sy_stages = 6;
-  m.sy_smem = m.sy_stages * 2 * kAStage + 1024 + 256;
   return m;
 }
 
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 152;
+}
+
 size_t mixed_workspace_bytes(int n, int naux, int nocc) {
-  const MixedPlan m = mixed_plan(n, naux, nocc);
-  size_t b = (size_t)m.ldx * m.ld * 4 + (size_t)n * m.ldx * 4;
-  b += (size_t)m.ncg * naux * n * 8 + (size_t)naux * 4;
-  b += (size_t)m.nchunk * m.ntri * kBM * kBM * 4;
-  b += (size_t)naux * n * (m.ldx - nocc) * 4;  // X32 padding beyond nocc
+  const MixedPlan m = mixed_plan(n, naux, nocc, 152);
+  size_t b = (size_t)naux * n * m.ld * 4;            // Bl (Bh counted by the caller)
+  b += (size_t)naux * n * (2 * m.ldx - nocc) * 4;    // Xh padding + Xl (Xh counted by caller)
+  b += (size_t)2 * m.ldx * m.ld * 4 + (size_t)n * m.ldx * 4;
+  b += (size_t)2 * m.ncg * naux * n * 4 + (size_t)naux * 4;
+  b += (size_t)m.nchunk * m.ntri * kBM * kBM * 8;
   return b;
 }
 
 struct MixedState {
   MixedPlan plan;
-  CUtensorMap mapA, mapB, mapX;
-  DBuf Cf, wrow, w32;
+  CUtensorMap mapAh, mapAl, mapCh, mapCl, mapXh, mapXl;
+  DBuf Bl, Xl, Cl, Cf, wpart, w32;
 };
 
 void MixedDeleter::operator()(MixedState *p) const { delete p; }
 
 int mixed_ld(int n) { return round_up(n, 4); }
 
+#define BQC_XN_LIST(X) X(32) X(64) X(96) X(128) X(160) X(192) X(224) X(256)
+
+static int dispatch_xn(int xn, int split, size_t smem, const XpassParams *p, const MixedState *ms,
+                       const CUtensorMap *Ah, const CUtensorMap *Al, int grid, cudaStream_t s) {
+#define BQC_XN_CASE(V)                                                                   \
+  case V:                                                                                \
+    if (split == 3) {                                                                    \
+      if (!p) {                                                                          \
+        BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<V, 3>,                            \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                          (int)smem));                                   \
+        return BQC_OK;                                                                   \
+      }                                                                                  \
+      k_xpass_tf32<V, 3><<<grid, kThreads, smem, s>>>(*Ah, *Al, ms->mapCh, ms->mapCl, *p); \
+    } else {                                                                             \
+      if (!p) {                                                                          \
+        BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<V, 1>,                            \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                          (int)smem));                                   \
+        return BQC_OK;                                                                   \
+      }                                                                                  \
+      k_xpass_tf32<V, 1><<<grid, kThreads, smem, s>>>(*Ah, *Ah, ms->mapCh, ms->mapCh, *p); \
+    }                                                                                    \
+    BQC_LAUNCH_CHECK();                                                                  \
+    return BQC_OK;
+  switch (xn) { BQC_XN_LIST(BQC_XN_CASE) }
+#undef BQC_XN_CASE
+  return BQC_E_UNSUPPORTED;
+}
+
 int mixed_setup(Df *df, cudaStream_t s) {
-  (void)s;
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux, no = b->nocc;
   MixedState *ms = new MixedState();
   df->mixed.reset(ms);
-  ms->plan = mixed_plan(n, naux, no);
+  ms->plan = mixed_plan(n, naux, no, sm_count());
   const MixedPlan &m = ms->plan;
-  if (m.xp_stages < 2) return BQC_E_UNSUPPORTED;
+  if (m.xp_stages[1] < 2 || m.sy_stages[1] < 2) return BQC_E_UNSUPPORTED;
   Ctx *ctx = df->ctx;
-  BQC_TRY(df->X32.alloc(ctx, (size_t)naux * n * m.ldx * 4));
-  BQC_TRY(df->Ct32.alloc(ctx, (size_t)m.ldx * m.ld * 4));
-  BQC_TRY(ms->Cf.alloc(ctx, (size_t)n * m.ldx * 4));
-  BQC_TRY(ms->wrow.alloc(ctx, (size_t)m.ncg * naux * n * 8));
-  BQC_TRY(ms->w32.alloc(ctx, (size_t)naux * 4));
-  BQC_TRY(df->Kpart.alloc(ctx, (size_t)m.nchunk * m.ntri * kBM * kBM * 4));
-  if (!df->Jp.p) BQC_TRY(df->Jp.alloc(ctx, (size_t)df->npair * 8));
-  // A: B32 as (Naux*N) rows x ld columns
+  // split shadow of B (Bh lives in df->B32, allocated by the caller)
+  BQC_TRY(ms->Bl.alloc(ctx, (size_t)naux * n * m.ld * 4));
   {
+    const int64_t tot = (int64_t)n * m.ld * naux;
+    k_expand_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        df->B64.as<double>(), n, m.ld, df->npair, 0, naux, df->B32.as<float>(), ms->Bl.as<float>());
+    BQC_LAUNCH_CHECK();
+  }
+  BQC_TRY(df->X32.alloc(ctx, (size_t)naux * n * m.ldx * 4));
+  BQC_TRY(ms->Xl.alloc(ctx, (size_t)naux * n * m.ldx * 4));
+  BQC_TRY(df->Ct32.alloc(ctx, (size_t)m.ldx * m.ld * 4));
+  BQC_TRY(ms->Cl.alloc(ctx, (size_t)m.ldx * m.ld * 4));
+  BQC_TRY(ms->Cf.alloc(ctx, (size_t)n * m.ldx * 4));
+  BQC_TRY(ms->wpart.alloc(ctx, (size_t)2 * m.ncg * naux * n * 4));
+  BQC_TRY(ms->w32.alloc(ctx, (size_t)naux * 4));
+  BQC_TRY(df->Kpart.alloc(ctx, (size_t)m.nchunk * m.ntri * kBM * kBM * 8));
+  if (!df->Jp.p) BQC_TRY(df->Jp.alloc(ctx, (size_t)df->npair * 8));
+  {  // A operands: B shadows as (Naux*N) rows x ld columns
     const uint64_t dims[2] = {(uint64_t)m.ld, (uint64_t)naux * n};
     const uint64_t str[1] = {(uint64_t)m.ld * 4};
     const uint32_t box[2] = {32, kBM};
-    BQC_TRY(make_tmap_f32(&ms->mapA, df->B32.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&ms->mapAh, df->B32.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&ms->mapAl, ms->Bl.p, 2, dims, str, box));
   }
-  // B: Ct32 as ldx rows x ld columns, boxes of sub_n rows
-  {
+  {  // B operands: C^T split as ldx rows x ld columns, boxes of xn rows
     const uint64_t dims[2] = {(uint64_t)m.ld, (uint64_t)m.ldx};
     const uint64_t str[1] = {(uint64_t)m.ld * 4};
-    const uint32_t box[2] = {32, (uint32_t)m.sub_n};
-    BQC_TRY(make_tmap_f32(&ms->mapB, df->Ct32.p, 2, dims, str, box));
+    const uint32_t box[2] = {32, (uint32_t)m.xn};
+    BQC_TRY(make_tmap_f32(&ms->mapCh, df->Ct32.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&ms->mapCl, ms->Cl.p, 2, dims, str, box));
   }
-  // X32 as (ldx, N, Naux)
-  {
+  {  // X split as (ldx, N, Naux)
     const uint64_t dims[3] = {(uint64_t)m.ldx, (uint64_t)n, (uint64_t)naux};
     const uint64_t str[2] = {(uint64_t)m.ldx * 4, (uint64_t)n * m.ldx * 4};
     const uint32_t box[3] = {32, kBM, 1};
-    BQC_TRY(make_tmap_f32(&ms->mapX, df->X32.p, 3, dims, str, box));
+    BQC_TRY(make_tmap_f32(&ms->mapXh, df->X32.p, 3, dims, str, box));
+    BQC_TRY(make_tmap_f32(&ms->mapXl, ms->Xl.p, 3, dims, str, box));
   }
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)m.xp_smem));
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)m.sy_smem));
+  for (int k = 0; k < 2; ++k)
+    BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, m.xp_smem[k], nullptr, ms, nullptr, nullptr, 0, s));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m.sy_smem[0]));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m.sy_smem[1]));
   return BQC_OK;
 }
 
-int mixed_xpass(Df *df, const double *C, cudaStream_t s, const CUtensorMap *mapA, int64_t rows,
-                float *X, double *w_out) {
+// X pass over `rows` rows of the A operands (Ah, Al), writing Xh / Xl and,
+// if w_out, the Coulomb contraction w.
+int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtensorMap *Ah,
+                const CUtensorMap *Al, int64_t rows, float *Xh, float *Xl, double *w_out) {
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
@@ -541,6 +791,7 @@ int mixed_xpass(Df *df, const double *C, cudaStream_t s, const CUtensorMap *mapA
   df->mark(0, s);
   k_prep_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, n, no, m.ld, m.ldx,
                                                           df->Ct32.as<float>(),
+                                                          split == 3 ? ms->Cl.as<float>() : nullptr,
                                                           ms->Cf.as<float>());
   BQC_LAUNCH_CHECK();
   df->mark(1, s);
@@ -548,30 +799,28 @@ int mixed_xpass(Df *df, const double *C, cudaStream_t s, const CUtensorMap *mapA
   p.rows = rows;
   p.n = n;
   p.ldx = m.ldx;
-  p.col0 = 0;
-  p.cols = m.cols;
-  p.sub_n = m.sub_n;
-  p.n_sub = m.n_sub;
+  p.ncg = m.ncg;
   p.kblocks = (m.ld + 31) / 32;
-  p.stages = m.xp_stages;
-  p.tmem_cols = 32;
-  while (p.tmem_cols < m.cols) p.tmem_cols *= 2;
-  p.X = X;
+  const int k = split == 3 ? 1 : 0;
+  p.stages = m.xp_stages[k];
+  p.tiles = (rows + kBM - 1) / kBM * m.ncg;
+  p.Xh = Xh;
+  p.Xl = Xl;
   p.Cf = ms->Cf.as<float>();
-  p.wrow = ms->wrow.as<double>();
+  p.wpart = ms->wpart.as<float>();
   p.flag = df->ctx->flag;
-  dim3 grid((unsigned)((rows + kBM - 1) / kBM), (unsigned)m.ncg);
-  k_xpass_tf32<<<grid, 128, m.xp_smem, s>>>(*mapA, ms->mapB, p);
-  BQC_LAUNCH_CHECK();
+  const int grid = (int)std::min<int64_t>(m.grid, p.tiles);
+  BQC_TRY(dispatch_xn(m.xn, split, m.xp_smem[k], &p, ms, Ah, Al, grid, s));
   if (w_out) {
-    k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wrow.as<double>(), rows, m.ncg, n, w_out,
-                                                    ms->w32.as<float>());
+    k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
+                                                    w_out, ms->w32.as<float>());
     BQC_LAUNCH_CHECK();
   }
   return BQC_OK;
 }
 
-int mixed_syrk(Df *df, const CUtensorMap *mapX, int naux, double *K, cudaStream_t s) {
+int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, int naux, double *K,
+               cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const int n = df->basis->nbf;
@@ -579,40 +828,51 @@ int mixed_syrk(Df *df, const CUtensorMap *mapX, int naux, double *K, cudaStream_
   q.n = n;
   q.ldx = m.ldx;
   q.naux = naux;
-  q.ntile = m.ntile;
   q.ntri = m.ntri;
   q.p_per_chunk = m.ppc;
+  q.nchunk = (naux + m.ppc - 1) / m.ppc;
   q.nib = m.ldx / 32;
-  q.stages = m.sy_stages;
-  q.part = df->Kpart.as<float>();
+  const int k = split == 3 ? 1 : 0;
+  q.stages = m.sy_stages[k];
+  q.part = df->Kpart.as<double>();
   q.flag = df->ctx->flag;
-  const int nchunk = (naux + m.ppc - 1) / m.ppc;
-  k_syrk_tf32<<<dim3((unsigned)m.ntri, (unsigned)nchunk), 128, m.sy_smem, s>>>(*mapX, q);
+  const int grid = std::min(m.grid, q.ntri * q.nchunk);
+  if (split == 3)
+    k_syrk_tf32<3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
+  else
+    k_syrk_tf32<1><<<grid, kThreads, m.sy_smem[0], s>>>(*Xh, *Xh, q);
   BQC_LAUNCH_CHECK();
-  k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(df->Kpart.as<float>(), nchunk,
+  k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(df->Kpart.as<double>(), q.nchunk,
                                                                   m.ntri, n, K);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
 }
 
-int jk_mixed_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {
+int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   if (!ms) return BQC_E_INVALID;
+  const int split = prec == BQC_PREC_MIXED_TF32X3 ? 3 : 1;
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux;
   const int64_t rows = (int64_t)naux * n;
-  BQC_TRY(mixed_xpass(df, C, s, &ms->mapA, rows, df->X32.as<float>(), df->w.as<double>()));
+  BQC_TRY(mixed_xpass(df, C, split, s, &ms->mapAh, &ms->mapAl, rows, df->X32.as<float>(),
+                      ms->Xl.as<float>(), df->w.as<double>()));
   df->mark(2, s);
-  // J pass (HBM-bound) over the lower triangle of B32
+  // J pass (HBM-bound) over the lower triangle of the B shadow
   const int threads = std::min(512, round_up((n - 1) / 4 + 3, 32));
-  k_jpass_tf32<<<(unsigned)((n + 1) / 2), threads, 0, s>>>(df->B32.as<float>(), ms->w32.as<float>(),
-                                                          naux, n, m.ld, df->Jp.as<double>());
+  if (split == 3)
+    k_jpass_tf32<3><<<(unsigned)((n + 1) / 2), threads, 0, s>>>(
+        df->B32.as<float>(), ms->Bl.as<float>(), ms->w32.as<float>(), naux, n, m.ld,
+        df->Jp.as<double>());
+  else
+    k_jpass_tf32<1><<<(unsigned)((n + 1) / 2), threads, 0, s>>>(
+        df->B32.as<float>(), nullptr, ms->w32.as<float>(), naux, n, m.ld, df->Jp.as<double>());
   BQC_LAUNCH_CHECK();
   k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(), n, J);
   BQC_LAUNCH_CHECK();
   df->mark(3, s);
-  BQC_TRY(mixed_syrk(df, &ms->mapX, naux, K, s));
+  BQC_TRY(mixed_syrk(df, split, &ms->mapXh, &ms->mapXl, naux, K, s));
   df->mark(4, s);
   return BQC_OK;
 }
