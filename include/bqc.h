@@ -169,6 +169,27 @@ int bqc_df_copy(const bqc_df *df, int which, double *out_dev, bqc_stream_t strea
 int bqc_jk(bqc_df *df, const double *C_occ_dev, int nocc, int prec, double *J_dev,
            double *K_dev, bqc_stream_t stream);
 
+/* Allocation-free FP64 Fock build (no counterpart in the paper; it exists
+ * for callers that cannot allocate device memory at call time, e.g. a host
+ * framework that has already reserved the GPU's memory in its own pool, or a
+ * latency-critical loop that cannot afford the device-wide synchronisation
+ * that cudaMalloc / cudaFree may cause).
+ * Computes the same J and K as bqc_jk with BQC_PREC_FP64 from caller-owned
+ * device buffers: B_dev is the packed FP64 B (Naux x Npair, as bqc_df_copy
+ * returns it), C_occ_dev N x nocc, J_dev and K_dev N x N.  Its working memory
+ * (Naux*N*nocc + Naux + Npair doubles, each part rounded up to 256 bytes) comes
+ * from a fixed array of BQC_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits; larger
+ * sizes return BQC_E_INVALID (bqc_last_error names the size) before any work.
+ * The first call on a device looks up that array's device address (one-time
+ * set-up, with the device current); make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose work overlaps
+ * on the GPU (different streams, or host threads without ordering) race and
+ * must be serialised by the caller.  Async. */
+#define BQC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int bqc_jk_fp64_noalloc(const double *B_dev, int naux, int nbf, const double *C_occ_dev,
+                        int nocc, double *J_dev, double *K_dev, bqc_stream_t stream);
+
 /* Same as bqc_jk with host buffers: copies C_occ in, J and K out, and
  * waits for the stream.  The end-to-end entry point. */
 int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, double *K,

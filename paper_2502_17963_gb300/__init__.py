@@ -111,6 +111,7 @@ _SIGS = {
     "bqc_df_copy": (ip, [vp, ip, vp, vp]),
     "bqc_jk": (ip, [vp, vp, ip, ip, vp, vp, vp]),
     "bqc_jk_host": (ip, [vp, vp, ip, ip, vp, vp, vp]),
+    "bqc_jk_fp64_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp, vp]),
     "bqc_df_timing": (ip, [vp, ip]),
     "bqc_df_phase_ms": (ip, [vp, ctypes.POINTER(ctypes.c_float), ip]),
     "bqc_scf_run": (ip, [vp, vp, ctypes.POINTER(bqc_scf_opts), vp,
