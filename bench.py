@@ -23,6 +23,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,6 +44,13 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving run: Poisson stream of (H2O)_n solves, p50/p99 latency")
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--direct", action="store_true",
+                    help="direct (on-the-fly) DF run, default (H2O)_128")
     return ap.parse_args()
 
 
@@ -168,8 +177,110 @@ def config(mol, prec):
             "parallelism": "replicas"}
 
 
+def run_serve(args):
+    """Continuous batching on the seeded Poisson stream (mean 20 req/s,
+    n ~ U{2..48}); the first --serve-requests requests, submitted at their
+    arrival times; latency = completion - arrival."""
+    import torch
+
+    import paper_2502_17963_gb300 as bqc
+    import workload
+    from paper_2502_17963_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    ctx = bqc.Context(0)
+    stream = workload.serving_stream(nreq=args.serve_requests, rate_hz=args.serve_rate)
+    out = {}
+    for prec, label in ((bqc.PREC_MIXED_TF32X3, "mixed_tf32x3"), (bqc.PREC_FP64, "fp64")):
+        srv = bqc.Server(ctx, max_slots=args.serve_slots, hbm_budget=150 * 10 ** 9, prec=prec)
+        clocks = ClockSampler(gpu_index(0))
+        clocks.start()
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, n, rid) in stream:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            mol = workload.water_cluster(n, seed=rid)
+            tickets.append((ta, n, srv.submit(mol)))
+        srv.drain(0)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        lat, ok, nbf = [], 0, []
+        for (ta, n, t) in tickets:
+            r = srv.poll(t)
+            lat.append(r["t_done"] - r["t_submit"])
+            ok += r["status"] == 0
+            nbf.append(r["nbf"])
+        srv.close()
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+        out[label] = {"p50_ms": q(0.5) * 1e3, "p99_ms": q(0.99) * 1e3, "solves_per_s": len(lat) / wall,
+                      "converged": ok, "requests": len(lat), "wall_s": wall, "clocks": clk,
+                      "offered_req_per_s": args.serve_rate}
+    line = {"metric": "serve p50/p99 ms (DF-RHF solves, Poisson arrivals)", "value": out["mixed_tf32x3"]["p99_ms"],
+            "unit": "ms (p99 latency)", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"Poisson {args.serve_rate} req/s, (H2O)_n n~U{{2..48}}, first "
+                                   f"{args.serve_requests} of the seed-2025 stream",
+                       "slots": args.serve_slots, "hbm_budget_gb": 150}, "serve": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_direct(args):
+    """Direct (on-the-fly) DF Fock build: s per build and its phases."""
+    import torch
+
+    import paper_2502_17963_gb300 as bqc
+    import workload
+    from paper_2502_17963_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    nw = args.waters if args.waters != 64 else 128
+    mol = workload.water_cluster(nw)
+    ctx = bqc.Context(0)
+    basis = bqc.Basis(ctx, mol)
+    t0 = time.perf_counter()
+    df = bqc.DF(ctx, basis, mode=bqc.DF_DIRECT, aux_block=1024, keep_fp32=True)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    C = torch.linalg.qr(torch.randn((basis.nbf, basis.nocc), dtype=torch.float64,
+                                    generator=torch.Generator().manual_seed(5)))[0].cuda() * 0.5
+    J = torch.empty((basis.nbf, basis.nbf), dtype=torch.float64, device="cuda")
+    K = torch.empty_like(J)
+    df.jk(C, bqc.PREC_MIXED_TF32X3, J, K)
+    torch.cuda.synchronize()
+    df.timing(True)
+    steps = max(1, min(args.steps, 3))
+    clocks = ClockSampler(gpu_index(0))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ph = []
+    for _ in range(steps):
+        df.jk(C, bqc.PREC_MIXED_TF32X3, J, K)
+        ph.append(df.phase_ms())
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    pm = np.mean(np.array(ph), axis=0).tolist()
+    line = {"metric": "s per Fock build, direct DF", "value": ms / 1e3, "unit": "s/build",
+            "n_gpus": 1, "steps": steps, "higher_is_better": False, "dtype": "f64 integrals, tf32x3",
+            "data": "synthetic", "config": {"workload": f"{mol.name} direct DF, N={basis.nbf}, "
+                                            f"Naux={basis.naux}, nocc={basis.nocc}, aux block 1024, "
+                                            "Schwarz 1e-10"},
+            "phases_ms": {"pass1_integrals_gamma_X": pm[0], "metric_solve_and_K": pm[1],
+                          "pass2_integrals_J": pm[2], "prep": pm[3]},
+            "setup_s": setup, "device_bytes": df.device_bytes, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
+    if args.direct:
+        return run_direct(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -198,7 +309,7 @@ def main():
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     # occupied orbitals of a physical state: two mixed SCF iterations from the core guess
-    r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32, max_iter=2, keep_arrays=True)
+    r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32X3, max_iter=2, keep_arrays=True)
     C = r["C"][:, :no].contiguous()
     J = torch.empty((n, n), dtype=torch.float64, device="cuda")
     K = torch.empty_like(J)

@@ -199,9 +199,11 @@ int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, 
  * every following bqc_jk on this handle record CUDA events at its phase
  * boundaries on its stream (leave it off while capturing a graph).
  * bqc_df_phase_ms waits for the last call's events and writes up to n
- * durations in ms: [0] X pass (X = B C with the fused w contraction),
- * [1] J pass, [2] K (SYRK and its FP64 reduction), [3] operand preparation
- * and unpacking.  BQC_E_NOT_READY if no timed call has been made. */
+ * durations in ms.  Stored mode: [0] X pass (X = B C with the fused w
+ * contraction), [1] J pass, [2] K (SYRK and its FP64 reduction), [3] operand
+ * preparation.  Direct mode: [0] first integral pass (integrals, gamma, X),
+ * [1] metric solve and K, [2] second integral pass (J), [3] preparation.
+ * BQC_E_NOT_READY if no timed call has been made. */
 int bqc_df_timing(bqc_df *df, int enable);
 int bqc_df_phase_ms(bqc_df *df, float *ms, int n);
 

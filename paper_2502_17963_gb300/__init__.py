@@ -388,3 +388,56 @@ def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
     if keep_arrays:
         out.update(C=Cbuf[: n * r.nmo].view(n, r.nmo), eps=eps[: r.nmo], F=F)
     return out
+
+
+class Server:
+    """bqc_server: continuous batching of SCF solves (see bqc_serve_create)."""
+
+    def __init__(self, ctx: Context, max_slots: int = 4, hbm_budget: int = 0,
+                 prec: int = PREC_MIXED_TF32X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
+                 stage_tol: float = 1e-5, max_iter: int = 100, diis_space: int = 8,
+                 orth_thresh: float = 1e-8):
+        self.ctx = ctx
+        o = bqc_serve_opts(max_slots, hbm_budget, prec,
+                           bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space,
+                                        prec, orth_thresh))
+        h = vp()
+        check(lib().bqc_serve_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "bqc_serve_create")
+        self.h = h
+
+    def submit(self, mol) -> int:
+        """Queues a solve of a workload.Molecule; returns its ticket."""
+        req, keep = molecule_request(mol)
+        t = ctypes.c_uint64()
+        check(lib().bqc_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), "bqc_serve_submit")
+        del keep  # the server copied the request
+        return t.value
+
+    def poll(self, ticket: int):
+        """Result dict once done, else None."""
+        r = bqc_serve_result()
+        st = lib().bqc_serve_poll(self.h, ticket, ctypes.byref(r))
+        if st == BQC_E_NOT_READY:
+            return None
+        check(st, "bqc_serve_poll")
+        return dict(status=r.status, energy=r.energy, diis_err=r.diis_err,
+                    iterations=r.iterations, nbf=r.nbf, t_submit=r.t_submit, t_admit=r.t_admit,
+                    t_done=r.t_done)
+
+    def drain(self, timeout_s: float = 0.0):
+        check(lib().bqc_serve_drain(self.h, timeout_s), "bqc_serve_drain")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bqc_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serve_footprint(nbf: int, naux: int, nocc: int) -> int:
+    return int(lib().bqc_serve_footprint(nbf, naux, nocc))

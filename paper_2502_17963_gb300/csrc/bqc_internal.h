@@ -153,6 +153,7 @@ struct Eri3cPlan {
   int64_t prefix_off[kNPairClass][kMaxLAux + 1] = {{0}};
   int64_t total[kNPairClass][kMaxLAux + 1] = {{0}};
   int64_t survivors = 0, candidates = 0;
+  std::vector<int64_t> h_prefix;  // host copy of d_prefix
 };
 // Builds the plan on `s` (one stream sync at the end to read the counts).
 int eri3c_plan(const Basis *b, double tau, const double *V_diag_dev, cudaStream_t s,

@@ -10,6 +10,10 @@ struct MixedState;
 struct MixedDeleter {
   void operator()(MixedState *p) const;
 };
+struct DirectMixed;
+struct DirectMixedDeleter {
+  void operator()(DirectMixed *p) const;
+};
 
 struct Df {
   Ctx *ctx = nullptr;
@@ -35,10 +39,13 @@ struct Df {
   std::unique_ptr<MixedState, MixedDeleter> mixed;  // plan, tensor maps, epilogue buffers
   // direct mode
   DBuf raw;    // aux block x Npair FP64 raw integrals
-  DBuf raw32;  // aux block x N x N TF32 (mixed)
-  DBuf Xraw;   // Naux x N x nocc (FP64 or FP32), then Y = L^{-1} X in place
-  DBuf gamma;  // Naux FP64
-  DBuf Jacc;   // Npair FP64
+  DBuf Linv;   // Naux x Naux FP64 L^{-1}
+  DBuf Xraw;   // FP64 path: Naux x N x nocc, then Y = L^{-1} X in place
+  DBuf gamma;  // Naux FP64: gamma_Q = (Q|D), then c = V^{-1} gamma
+  DBuf D2;     // Npair FP64 packed density, off-diagonal doubled
+  DBuf Kpart64;
+  int aux_block = 1024;
+  std::unique_ptr<DirectMixed, DirectMixedDeleter> dmixed;  // tensor-core state
   // phase timing (bqc_df_timing)
   bool timing = false, timed = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -51,7 +58,7 @@ struct Df {
   }
   size_t device_bytes() const {
     return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +
-           wpart.n + Kpart.n + raw.n + raw32.n + Xraw.n + gamma.n + Jacc.n +
+           wpart.n + Kpart.n + raw.n + Linv.n + Xraw.n + gamma.n + D2.n +
            plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n;
   }
 };
@@ -62,6 +69,11 @@ int mixed_setup(Df *df, cudaStream_t s);
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 int direct_setup(Df *df, cudaStream_t s);
+size_t direct_mixed_bytes(int n, int naux, int nocc, int bs);
+int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s);
+int direct_mixed_prep_c(Df *df, const double *C, int split, cudaStream_t s);
+int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cudaStream_t s);
+int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s);
 int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 size_t df_stored_bytes(int n, int naux, int nocc, bool fp32);
 

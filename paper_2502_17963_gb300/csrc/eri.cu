@@ -524,7 +524,10 @@ __global__ void __launch_bounds__(256) k_eri3c(Eri3cArgs a) {
   const int group_in_block = threadIdx.x / G;
   const int groups_per_block = blockDim.x / G;
   double *scr = smem + (size_t)group_in_block * O::SCR;
-  const int64_t total = a.prefix[a.n_aux];
+  // triplet index space of this launch: [prefix[0], prefix[n_aux]) (a window
+  // of aux shells may start past the first shell of the l-list)
+  const int64_t pbase = a.prefix[0];
+  const int64_t total = a.prefix[a.n_aux] - pbase;
   const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
   // warp-uniform trip count: all groups of a warp iterate together
   const int warp_first_group = (threadIdx.x >> 5) * (32 / G);
@@ -533,6 +536,7 @@ __global__ void __launch_bounds__(256) k_eri3c(Eri3cArgs a) {
     int64_t t = base + (group_in_block - warp_first_group);
     const bool active = t < total;
     if (!active) t = total - 1;
+    t += pbase;
     // aux shell: largest i with prefix[i] <= t
     int lo = 0, hi = a.n_aux;
     while (hi - lo > 1) {
@@ -620,24 +624,44 @@ int launch_eri3c(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *
   for (int lc = 0; lc <= kMaxLAux; ++lc) {
     const int na = b->auxl_off[lc + 1] - b->auxl_off[lc];
     if (na == 0) continue;
+    // shells of this l whose functions meet [p0, p1): a contiguous sub-range
+    // [s0, s1) of the l-list, since function offsets grow with shell index
+    int s0 = 0, s1 = 0;
+    {
+      int k = 0;
+      s0 = -1;
+      for (int sh = 0; sh < (int)b->aux.l.size(); ++sh) {
+        if (b->aux.l[sh] != lc) continue;
+        const int f0 = b->aux.fn[sh], f1 = f0 + (lc + 1) * (lc + 2) / 2;
+        if (f1 > p0 && f0 < p1) {
+          if (s0 < 0) s0 = k;
+          s1 = k + 1;
+        }
+        ++k;
+      }
+      if (s0 < 0) continue;
+    }
     for (int cls = 0; cls < kNPairClass; ++cls) {
       const int np = b->pair_off[cls + 1] - b->pair_off[cls];
       if (np == 0 || plan->total[cls][lc] == 0) continue;
+      const int64_t *hp = plan->h_prefix.data() + plan->prefix_off[cls][lc];
+      const int64_t ntrip = hp[s1] - hp[s0];
+      if (ntrip == 0) continue;
       Eri3cArgs a;
       a.orb = b->orb.dev;
       a.aux = b->aux.dev;
       a.boys = b->ctx->boys;
       a.pairs = plan->d_pairs_sorted.as<int2>() + b->pair_off[cls];
-      a.aux_list = b->d_aux_by_l.as<int>() + b->auxl_off[lc];
-      a.prefix = plan->d_prefix.as<int64_t>() + plan->prefix_off[cls][lc];
-      a.n_aux = na;
+      a.aux_list = b->d_aux_by_l.as<int>() + b->auxl_off[lc] + s0;
+      a.prefix = plan->d_prefix.as<int64_t>() + plan->prefix_off[cls][lc] + s0;
+      a.n_aux = s1 - s0;
       a.p0 = p0;
       a.p1 = p1;
       a.out = out;
       a.ld = ld;
       a.flag = b->ctx->flag;
       a.out_elems = (int64_t)(p1 - p0) * ld;
-      BQC_TRY(dispatch3(lc, cls, a, plan->total[cls][lc], s));
+      BQC_TRY(dispatch3(lc, cls, a, ntrip, s));
     }
   }
   return BQC_OK;
@@ -1115,7 +1139,8 @@ int eri3c_plan(const Basis *b, double tau, const double *V_diag_dev, cudaStream_
     }
   }
   // read the totals (one small copy)
-  std::vector<int64_t> h(off);
+  std::vector<int64_t> &h = plan->h_prefix;
+  h.assign(off, 0);
   BQC_CUDA_TRY(cudaMemcpyAsync(h.data(), plan->d_prefix.p, off * sizeof(int64_t),
                                cudaMemcpyDeviceToHost, s));
   BQC_CUDA_TRY(cudaStreamSynchronize(s));

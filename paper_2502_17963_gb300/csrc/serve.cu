@@ -1,14 +1,353 @@
-// Serving loop: placeholder until the continuous-batching server lands.
+// Continuous-batching server for DF-RHF solves (the serving workload).
+//
+// Requests of different molecule sizes arrive at any time.  A request is
+// admitted as soon as a slot is free and the HBM ledger has room for its
+// predicted footprint; every admitted request runs its basis setup, DF build
+// and SCF on its own CUDA stream, so the work of several molecules overlaps
+// on the device while new requests keep arriving.  All device memory comes
+// from one arena reserved when the server is created, so the serving loop
+// never calls cudaMalloc / cudaFree (both can synchronise the device and
+// would serialise the slots).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "bqc_internal.h"
+#include "df_internal.h"
+
+namespace bqc {
+
+// ------------------------------------------------------------- arena ----
+
+// First-fit sub-allocator over one device allocation; blocks are 256-byte
+// aligned and neighbouring free blocks are merged on release.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0;
+  std::mutex mu;
+  std::map<size_t, size_t> free_;   // offset -> size
+  std::unordered_map<size_t, size_t> used_;
+  size_t in_use = 0, peak = 0;
+
+  int init(size_t bytes) {
+    size = (bytes + 255) & ~(size_t)255;
+    if (cudaMalloc(&base, size) != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      set_error("arena reservation failed", __FILE__, __LINE__);
+      return BQC_E_OOM;
+    }
+    free_[0] = size;
+    return BQC_OK;
+  }
+  ~Arena() {
+    if (base) cudaFree(base);
+  }
+  void *alloc(size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    std::lock_guard<std::mutex> g(mu);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const size_t off = it->first, rest = it->second - bytes;
+      free_.erase(it);
+      if (rest) free_[off + bytes] = rest;
+      used_[off] = bytes;
+      in_use += bytes;
+      peak = std::max(peak, in_use);
+      return base + off;
+    }
+    return nullptr;
+  }
+  void release(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(mu);
+    const size_t off = (size_t)((char *)p - base);
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t sz = u->second;
+    used_.erase(u);
+    in_use -= sz;
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + sz) {
+      sz += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == start) {
+        start = pv->first;
+        sz += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[start] = sz;
+  }
+};
+
+static void *arena_alloc(size_t bytes, void *user) { return static_cast<Arena *>(user)->alloc(bytes); }
+static void arena_free(void *p, void *user) { static_cast<Arena *>(user)->release(p); }
+
+// ------------------------------------------------------------ requests --
+
+struct Request {
+  uint64_t id = 0;
+  std::vector<int> Z;
+  std::vector<double> xyz;
+  std::vector<int> shl_atom[2], shl_l[2], shl_np[2];
+  std::vector<double> exps[2], coefs[2];
+  int nbf = 0, naux = 0, nocc = 0;
+  size_t footprint = 0;
+  bool done = false;
+  bqc_serve_result res{};
+};
+
+static int ncart_s(int l) { return (l + 1) * (l + 2) / 2; }
+
+}  // namespace bqc
+
+struct bqc_server {
+  bqc::Ctx *outer = nullptr;
+  bqc_ctx *ctx = nullptr;  // internal context allocating from the arena
+  bqc::Arena arena;
+  bqc_serve_opts opts{};
+  size_t budget = 0, ledger = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<bqc::Request>> reqs;
+  std::vector<std::thread> workers;
+  uint64_t next_id = 1;
+  int pending = 0;
+  bool stop = false;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace bqc {
+
+// Predicted device bytes of one solve: stored DF tensors (FP64 B, split TF32
+// shadows, X), the integral screening plan, and the SCF work matrices.
+size_t serve_footprint(int n, int naux, int nocc, bool mixed) {
+  const size_t nn = (size_t)n * n;
+  size_t b = df_stored_bytes(n, naux, nocc, mixed);
+  b += (size_t)naux * naux * 8;             // metric copy during the build
+  b += (size_t)(16 + 2 * 8) * nn * 8;       // SCF matrices + DIIS history
+  b += (size_t)3 * n * n / 2 * 16;          // shell-pair plan (generous)
+  b += (size_t)64 << 20;                    // Boys table, small buffers, alignment
+  return b;
+}
+
+static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
+  std::vector<bqc_shell> sh[2];
+  for (int k = 0; k < 2; ++k) {
+    size_t po = 0;
+    for (size_t i = 0; i < r->shl_l[k].size(); ++i) {
+      sh[k].push_back(bqc_shell{r->shl_atom[k][i], r->shl_l[k][i], r->shl_np[k][i],
+                                r->exps[k].data() + po, r->coefs[k].data() + po});
+      po += r->shl_np[k][i];
+    }
+  }
+  bqc_basis *basis = nullptr;
+  bqc_df *df = nullptr;
+  int st = bqc_basis_load(srv->ctx, (int)r->Z.size(), r->Z.data(), r->xyz.data(), sh[0].data(),
+                          (int)sh[0].size(), sh[1].data(), (int)sh[1].size(), &basis);
+  bqc_scf_result res{};
+  if (st == BQC_OK) {
+    bqc_df_opts o{};
+    o.mode = BQC_DF_STORED;
+    o.schwarz = -1.0;
+    o.aux_block = 1024;
+    o.keep_fp32 = srv->opts.prec != BQC_PREC_FP64;
+    o.hbm_limit = 0;
+    st = bqc_df_build(srv->ctx, basis, &o, (bqc_stream_t)s, &df);
+  }
+  if (st == BQC_OK) {
+    bqc_scf_opts so = srv->opts.scf;
+    so.prec = srv->opts.prec;
+    st = bqc_scf_run(srv->ctx, df, &so, (bqc_stream_t)s, &res);
+  }
+  // the stream is idle now: free without the device-wide synchronisation of
+  // the public destroy calls, which would stall the other slots
+  cudaStreamSynchronize(s);
+  delete df;
+  delete basis;
+  r->res.status = st;
+  r->res.energy = res.energy;
+  r->res.diis_err = res.diis_err;
+  r->res.iterations = res.iterations;
+}
+
+static void worker_main(bqc_server *srv) {
+  cudaSetDevice(srv->ctx->device);
+  cudaStream_t s;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  while (true) {
+    Request *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_work.wait(lk, [&] {
+        if (srv->stop) return true;
+        if (srv->queue.empty()) return false;
+        Request *h = srv->reqs[srv->queue.front()].get();
+        return srv->ledger + h->footprint <= srv->budget;  // FIFO admission by HBM ledger
+      });
+      if (srv->stop && srv->queue.empty()) break;
+      if (srv->stop) break;
+      r = srv->reqs[srv->queue.front()].get();
+      srv->queue.pop_front();
+      srv->ledger += r->footprint;
+      r->res.t_admit = srv->now();
+    }
+    run_request(srv, r, s);
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->ledger -= r->footprint;
+      r->res.t_done = srv->now();
+      r->done = true;
+      --srv->pending;
+    }
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+  }
+  cudaStreamDestroy(s);
+}
+
+}  // namespace bqc
+
+using namespace bqc;
 
 extern "C" {
-int bqc_serve_create(bqc_ctx *, const bqc_serve_opts *, bqc_server **out) {
-  if (out) *out = nullptr;
-  return BQC_E_UNSUPPORTED;
+
+size_t bqc_serve_footprint(int nbf, int naux, int nocc) {
+  if (nbf <= 0 || naux <= 0 || nocc <= 0) return 0;
+  return serve_footprint(nbf, naux, nocc, true);
 }
-int bqc_serve_submit(bqc_server *, const bqc_request *, uint64_t *) { return BQC_E_UNSUPPORTED; }
-int bqc_serve_poll(bqc_server *, uint64_t, bqc_serve_result *) { return BQC_E_UNSUPPORTED; }
-int bqc_serve_drain(bqc_server *, double) { return BQC_E_UNSUPPORTED; }
-int bqc_serve_destroy(bqc_server *) { return BQC_E_UNSUPPORTED; }
-size_t bqc_serve_footprint(int, int, int) { return 0; }
+
+int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out) {
+  if (!ctx || !out) return BQC_E_INVALID;
+  *out = nullptr;
+  BQC_CUDA_TRY(cudaSetDevice(ctx->device));
+  std::unique_ptr<bqc_server> srv(new bqc_server());
+  srv->outer = ctx;
+  bqc_serve_opts o{};
+  o.max_slots = 4;
+  o.hbm_budget = 0;
+  o.prec = BQC_PREC_MIXED_TF32X3;
+  o.scf.diis_tol = 1e-8;
+  o.scf.energy_tol = 1e-10;
+  o.scf.stage_tol = 1e-5;
+  o.scf.max_iter = 100;
+  o.scf.diis_space = 8;
+  o.scf.orth_thresh = 1e-8;
+  if (opts) o = *opts;
+  if (o.max_slots <= 0) o.max_slots = 4;
+  srv->opts = o;
+  size_t budget = o.hbm_budget ? o.hbm_budget : ctx->budget;
+  if (!budget) {
+    size_t fr = 0, tot = 0;
+    BQC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    budget = fr / 2;
+  }
+  srv->budget = budget;
+  BQC_TRY(srv->arena.init(budget + ((size_t)64 << 20)));
+  bqc_ctx *ic = nullptr;
+  BQC_TRY(bqc_ctx_create(ctx->device, budget, arena_alloc, arena_free, &srv->arena, &ic));
+  srv->ctx = ic;
+  srv->t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < o.max_slots; ++i) srv->workers.emplace_back(worker_main, srv.get());
+  *out = srv.release();
+  return BQC_OK;
 }
+
+int bqc_serve_submit(bqc_server *srv, const bqc_request *q, uint64_t *ticket) {
+  if (!srv || !q || !ticket || q->natom <= 0 || !q->Z || !q->xyz_bohr || !q->orb || !q->aux)
+    return BQC_E_INVALID;
+  std::unique_ptr<Request> r(new Request());
+  r->Z.assign(q->Z, q->Z + q->natom);
+  r->xyz.assign(q->xyz_bohr, q->xyz_bohr + 3 * q->natom);
+  int zsum = 0;
+  for (int z : r->Z) zsum += z;
+  const bqc_shell *lists[2] = {q->orb, q->aux};
+  const int counts[2] = {q->norb_shell, q->naux_shell};
+  int nf[2] = {0, 0};
+  for (int k = 0; k < 2; ++k) {
+    if (counts[k] <= 0) return BQC_E_INVALID;
+    for (int i = 0; i < counts[k]; ++i) {
+      const bqc_shell &s = lists[k][i];
+      if (s.nprim <= 0 || s.nprim > kMaxPrim || !s.exps || !s.coefs) return BQC_E_INVALID;
+      r->shl_atom[k].push_back(s.atom);
+      r->shl_l[k].push_back(s.l);
+      r->shl_np[k].push_back(s.nprim);
+      r->exps[k].insert(r->exps[k].end(), s.exps, s.exps + s.nprim);
+      r->coefs[k].insert(r->coefs[k].end(), s.coefs, s.coefs + s.nprim);
+      nf[k] += ncart_s(s.l);
+    }
+  }
+  r->nbf = nf[0];
+  r->naux = nf[1];
+  r->nocc = zsum / 2;
+  r->footprint = serve_footprint(r->nbf, r->naux, std::max(1, r->nocc),
+                                 srv->opts.prec != BQC_PREC_FP64);
+  if (r->footprint > srv->budget) return BQC_E_ADMISSION;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  r->id = srv->next_id++;
+  r->res.status = BQC_E_NOT_READY;
+  r->res.nbf = r->nbf;
+  r->res.t_submit = srv->now();
+  *ticket = r->id;
+  srv->queue.push_back(r->id);
+  ++srv->pending;
+  srv->reqs[r->id] = std::move(r);
+  srv->cv_work.notify_all();
+  return BQC_OK;
+}
+
+int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res) {
+  if (!srv || !res) return BQC_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return BQC_E_INVALID;
+  if (!it->second->done) return BQC_E_NOT_READY;
+  *res = it->second->res;
+  return BQC_OK;
+}
+
+int bqc_serve_drain(bqc_server *srv, double timeout_s) {
+  if (!srv) return BQC_E_INVALID;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto pred = [&] { return srv->pending == 0; };
+  if (timeout_s <= 0) {
+    srv->cv_done.wait(lk, pred);
+    return BQC_OK;
+  }
+  const bool ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred);
+  return ok ? BQC_OK : BQC_E_TIMEOUT;
+}
+
+int bqc_serve_destroy(bqc_server *srv) {
+  if (!srv) return BQC_E_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto &t : srv->workers) t.join();
+  if (srv->ctx) bqc_ctx_destroy(srv->ctx);
+  delete srv;
+  return BQC_OK;
+}
+
+}  // extern "C"

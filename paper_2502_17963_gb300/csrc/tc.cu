@@ -116,11 +116,17 @@ struct XpassParams {
   const float *Cf;   // N x ldx, fp32 C_occ
   float *wpart;      // [2 * ncg][rows] partial w per row
   int *flag;
+  // transposed epilogue (EPI = 1, direct mode): rows are (mu, q) with q the
+  // aux function within a block of bk, written to X^T[mu][i][q0 + q] with
+  // row length naux_ld
+  int bk, q0, bkv;   // bkv: valid rows per mu (a ragged last sub-block)
+  int64_t naux_ld;
 };
 
 // Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
 // t / ncg, column group t % ncg), so neighbouring CTAs share A rows in L2.
-template <int XN, int SPLIT>
+// EPI 0: X[row][i] (hi/lo) and the fused w_P partials; EPI 1: X^T layout.
+template <int XN, int SPLIT, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_xpass_tf32(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
                  const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
       const int64_t row = m0 + q * 32 + lane;
-      if (ok && row < p.rows) {
+      if (EPI == 0 && ok && row < p.rows) {
         const int mu = (int)(row % p.n);
         const int col = cg * XN + h * HALF;
         float *xh = p.Xh + row * p.ldx + col;
@@ -274,6 +280,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum;
+      }
+      if (EPI == 1 && ok && row < p.rows && (int)(row % p.bk) < p.bkv) {
+        // consecutive lanes hold consecutive q of one mu: coalesced per column
+        const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
+        const int col = cg * XN + h * HALF;
+        const int64_t base = (mu * p.ldx + col) * p.naux_ld + qq;
+#pragma unroll
+        for (int c = 0; c < HALF; ++c) {
+          const float hv = tf32r(acc[c]);
+          p.Xh[base + (int64_t)c * p.naux_ld] = hv;
+          if (SPLIT == 3) p.Xl[base + (int64_t)c * p.naux_ld] = tf32r(acc[c] - hv);
+        }
       }
     }
   }
@@ -312,6 +330,11 @@ struct SyrkParams {
   int stages;
   double *part;  // [chunk][ntri][128][128]
   int *flag;
+  // 2-D operand mode (direct mode): X^T as rows mu x K with K = (i, P)
+  // contiguous; chunks are ranges of kb_per_chunk k-blocks of kb_total
+  int mode2d;
+  int64_t kb_total;
+  int64_t kb_per_chunk;
 };
 
 __device__ __forceinline__ void tile_of(int t, int &tm, int &tn) {
@@ -360,15 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tbase = *tslot;
   const uint32_t sbase = smem_u32(smem);
   bool ok = true;
-  auto chunk_kb = [&](int ch, int &P0, int &nkb) {
-    P0 = ch * p.p_per_chunk;
-    nkb = max(0, min(p.naux, P0 + p.p_per_chunk) - P0) * p.nib;
+  // chunk ch -> first aux function P0 (3-D mode) or first k-block (2-D mode), k-block count
+  auto chunk_kb = [&](int ch, int64_t &P0, int &nkb) {
+    if (p.mode2d) {
+      P0 = (int64_t)ch * p.kb_per_chunk;
+      nkb = (int)max((int64_t)0, min(p.kb_total, P0 + p.kb_per_chunk) - P0);
+    } else {
+      P0 = (int64_t)ch * p.p_per_chunk;
+      nkb = max(0, min(p.naux, (int)P0 + p.p_per_chunk) - (int)P0) * p.nib;
+    }
   };
   if (warp == 0) {
     if (lane == 0) {
       int64_t kg = 0;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        int tm, tn, P0, nkb;
+        int tm, tn, nkb;
+        int64_t P0;
         tile_of(it % p.ntri, tm, tn);
         chunk_kb(it / p.ntri, P0, nkb);
         for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
@@ -376,14 +406,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (kg >= p.stages)
             ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 21);
           if (!ok) break;
-          const int P = P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
           const uint32_t a = sbase + s * stage_bytes, bar = full0 + 8 * s;
           mbar_arrive_expect_tx(bar, stage_bytes);
-          tma_load_3d(a, &mapXh, bar, i0, tm * kBM, P);
-          tma_load_3d(a + kAStage, &mapXh, bar, i0, tn * kBM, P);
-          if (SPLIT == 3) {
-            tma_load_3d(a + 2 * kAStage, &mapXl, bar, i0, tm * kBM, P);
-            tma_load_3d(a + 3 * kAStage, &mapXl, bar, i0, tn * kBM, P);
+          if (p.mode2d) {
+            const int k0 = (int)((P0 + kb) * 32);
+            tma_load_2d(a, &mapXh, bar, k0, tm * kBM);
+            tma_load_2d(a + kAStage, &mapXh, bar, k0, tn * kBM);
+            if (SPLIT == 3) {
+              tma_load_2d(a + 2 * kAStage, &mapXl, bar, k0, tm * kBM);
+              tma_load_2d(a + 3 * kAStage, &mapXl, bar, k0, tn * kBM);
+            }
+          } else {
+            const int P = (int)P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
+            tma_load_3d(a, &mapXh, bar, i0, tm * kBM, P);
+            tma_load_3d(a + kAStage, &mapXh, bar, i0, tn * kBM, P);
+            if (SPLIT == 3) {
+              tma_load_3d(a + 2 * kAStage, &mapXl, bar, i0, tm * kBM, P);
+              tma_load_3d(a + 3 * kAStage, &mapXl, bar, i0, tn * kBM, P);
+            }
           }
         }
       }
@@ -393,7 +433,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_tf32(kBM, kBM);
       int64_t kg = 0, g = 0;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        int P0, nkb;
+        int nkb;
+        int64_t P0;
         chunk_kb(it / p.ntri, P0, nkb);
         for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKb, ++g) {
           const int b = (int)(g & 1);
@@ -429,7 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     int64_t g = 0;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
-      int P0, nkb;
+      int nkb;
+      int64_t P0;
       chunk_kb(it / p.ntri, P0, nkb);
       float hi[kSyCols];
 #pragma unroll
@@ -516,6 +558,174 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nch
     const int mu = tm * kBM + sr * 32 + rr, nu = tn * kBM + c;
     if (mu < n && nu < n && (tm != tn || nu < mu)) K[(int64_t)nu * n + mu] = strip[rr][c];
   }
+}
+
+// ---------------------------------------------------------------- TRMM ---
+
+// In-place Y = X L^{-T} on the rows of X^T:  Y[r][P] = sum_{Q <= P} X[r][Q] Linv[P][Q]
+// (r = (mu, i), so Y^T holds the metric-orthogonalised Y_P = (L^{-1} X)_P of
+// direct mode).  A CTA owns row tiles exclusively and walks the P tiles of a
+// row tile from the last to the first: tile pt reads columns Q < (pt+1)*128
+// and writes columns [pt*128, pt*128+128), which later (smaller) tiles never
+// read, so the product can overwrite X.
+struct TrmmParams {
+  int64_t rows;      // N * ldx
+  int naux;          // columns (P and Q)
+  int64_t ld;        // row length of X (= naux)
+  int ntp;           // P tiles of 128
+  int stages;
+  int64_t mtiles;
+  float *Xh, *Xl;
+  int *flag;
+};
+
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_trmm_tf32(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
+                const __grid_constant__ CUtensorMap mapLh, const __grid_constant__ CUtensorMap mapLl,
+                const TrmmParams p) {
+  constexpr int NS = SPLIT == 3 ? 2 : 1;
+  constexpr uint32_t stage_bytes = NS * 2 * kAStage;  // [Xh][Lh][Xl][Ll]
+  constexpr int HALF = kBM / 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
+  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapXh);
+    prefetch_tmap(&mapLh);
+    if (SPLIT == 3) {
+      prefetch_tmap(&mapXl);
+      prefetch_tmap(&mapLl);
+    }
+    for (int st = 0; st < p.stages; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tslot), 256);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t sbase = smem_u32(smem);
+  auto kblocks_of = [&](int pt) { return (min(p.naux, (pt + 1) * kBM) + 31) / 32; };
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t kg = 0;
+      for (int64_t t = blockIdx.x; t < p.mtiles && ok; t += gridDim.x) {
+        const int m0 = (int)(t * kBM);
+        for (int pt = p.ntp - 1; pt >= 0 && ok; --pt) {
+          const int nkb = kblocks_of(pt);
+          for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
+            const int st = (int)(kg % p.stages);
+            if (kg >= p.stages)
+              ok = mbar_wait(empty0 + 8 * st, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 31);
+            if (!ok) break;
+            const uint32_t a = sbase + st * stage_bytes, bar = full0 + 8 * st;
+            mbar_arrive_expect_tx(bar, stage_bytes);
+            tma_load_2d(a, &mapXh, bar, kb * 32, m0);
+            tma_load_2d(a + kAStage, &mapLh, bar, kb * 32, pt * kBM);
+            if (SPLIT == 3) {
+              tma_load_2d(a + 2 * kAStage, &mapXl, bar, kb * 32, m0);
+              tma_load_2d(a + 3 * kAStage, &mapLl, bar, kb * 32, pt * kBM);
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kBM, kBM);
+      int64_t kg = 0, g = 0;
+      for (int64_t t = blockIdx.x; t < p.mtiles && ok; t += gridDim.x) {
+        for (int pt = p.ntp - 1; pt >= 0 && ok; --pt) {
+          const int nkb = kblocks_of(pt);
+          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKb, ++g) {
+            const int b = (int)(g & 1);
+            if (g >= 2)
+              ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 34);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tbase + b * kBM;
+            const int kb1 = min(nkb, kb0 + kGroupKb);
+            for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
+              const int st = (int)(kg % p.stages);
+              ok = mbar_wait(full0 + 8 * st, (uint32_t)((kg / p.stages) & 1), p.flag, 32);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t xh = sbase + st * stage_bytes, lh = xh + kAStage;
+              const uint32_t xl = xh + 2 * kAStage, ll = xh + 3 * kAStage;
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint32_t first = ((kb - kb0) | k4) != 0;
+                mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, first);
+                if (SPLIT == 3) {
+                  mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(ll + k4 * 32), idesc, 1);
+                  mma_tf32(d, sdesc_sw128(xl + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, 1);
+                }
+              }
+              mma_commit(empty0 + 8 * st);
+            }
+            mma_commit(tfull0 + 8 * b);
+          }
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    int64_t g = 0;
+    for (int64_t t = blockIdx.x; t < p.mtiles; t += gridDim.x) {
+      for (int pt = p.ntp - 1; pt >= 0; --pt) {
+        const int nkb = kblocks_of(pt);
+        float acc[HALF];
+#pragma unroll
+        for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
+        for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKb, ++g) {
+          const int b = (int)(g & 1);
+          if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 33);
+          __syncwarp();
+          tc_fence_after();
+          const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * kBM + h * HALF;
+#pragma unroll
+          for (int c = 0; c < HALF; c += 16) {
+            float v[16];
+            tmem_ld16(ta + c, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+        }
+        const int64_t row = t * kBM + q * 32 + lane;
+        const int col0 = pt * kBM + h * HALF;
+        if (ok && row < p.rows) {
+          float *yh = p.Xh + row * p.ld + col0;
+          float *yl = p.Xl + row * p.ld + col0;
+#pragma unroll
+          for (int c = 0; c < HALF; ++c) {
+            if (col0 + c < p.naux) {
+              const float hv = tf32r(acc[c]);
+              yh[c] = hv;
+              if (SPLIT == 3) yl[c] = tf32r(acc[c] - hv);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 256);
 }
 
 // -------------------------------------------------------------- J pass ---
@@ -695,29 +905,38 @@ int mixed_ld(int n) { return round_up(n, 4); }
 
 #define BQC_XN_LIST(X) X(32) X(64) X(96) X(128) X(160) X(192) X(224) X(256)
 
-static int dispatch_xn(int xn, int split, size_t smem, const XpassParams *p, const MixedState *ms,
-                       const CUtensorMap *Ah, const CUtensorMap *Al, int grid, cudaStream_t s) {
-#define BQC_XN_CASE(V)                                                                   \
-  case V:                                                                                \
-    if (split == 3) {                                                                    \
-      if (!p) {                                                                          \
-        BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<V, 3>,                            \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                          (int)smem));                                   \
-        return BQC_OK;                                                                   \
-      }                                                                                  \
-      k_xpass_tf32<V, 3><<<grid, kThreads, smem, s>>>(*Ah, *Al, ms->mapCh, ms->mapCl, *p); \
-    } else {                                                                             \
-      if (!p) {                                                                          \
-        BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<V, 1>,                            \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                          (int)smem));                                   \
-        return BQC_OK;                                                                   \
-      }                                                                                  \
-      k_xpass_tf32<V, 1><<<grid, kThreads, smem, s>>>(*Ah, *Ah, ms->mapCh, ms->mapCh, *p); \
-    }                                                                                    \
-    BQC_LAUNCH_CHECK();                                                                  \
+template <int XN, int SPLIT, int EPI>
+static int xpass_run(size_t smem, const XpassParams *p, const CUtensorMap *Ah,
+                     const CUtensorMap *Al, const CUtensorMap *Ch, const CUtensorMap *Cl, int grid,
+                     cudaStream_t s) {
+  if (!p) {
+    BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<XN, SPLIT, EPI>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return BQC_OK;
+  }
+  k_xpass_tf32<XN, SPLIT, EPI><<<grid, kThreads, smem, s>>>(*Ah, *Al, *Ch, *Cl, *p);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+template <int XN>
+static int xpass_split_epi(int split, int epi, size_t smem, const XpassParams *p,
+                           const CUtensorMap *Ah, const CUtensorMap *Al, const CUtensorMap *Ch,
+                           const CUtensorMap *Cl, int grid, cudaStream_t s) {
+  if (split == 3)
+    return epi ? xpass_run<XN, 3, 1>(smem, p, Ah, Al, Ch, Cl, grid, s)
+               : xpass_run<XN, 3, 0>(smem, p, Ah, Al, Ch, Cl, grid, s);
+  return epi ? xpass_run<XN, 1, 1>(smem, p, Ah, Ah, Ch, Ch, grid, s)
+             : xpass_run<XN, 1, 0>(smem, p, Ah, Ah, Ch, Ch, grid, s);
+}
+
+// p == nullptr: only set the kernel's shared-memory attribute.
+static int dispatch_xn(int xn, int split, int epi, size_t smem, const XpassParams *p,
+                       const CUtensorMap *Ah, const CUtensorMap *Al, const CUtensorMap *Ch,
+                       const CUtensorMap *Cl, int grid, cudaStream_t s) {
+#define BQC_XN_CASE(V) \
+  case V:              \
+    return xpass_split_epi<V>(split, epi, smem, p, Ah, Al, Ch, Cl, grid, s);
   switch (xn) { BQC_XN_LIST(BQC_XN_CASE) }
 #undef BQC_XN_CASE
   return BQC_E_UNSUPPORTED;
@@ -771,7 +990,9 @@ int mixed_setup(Df *df, cudaStream_t s) {
     BQC_TRY(make_tmap_f32(&ms->mapXl, ms->Xl.p, 3, dims, str, box));
   }
   for (int k = 0; k < 2; ++k)
-    BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, m.xp_smem[k], nullptr, ms, nullptr, nullptr, 0, s));
+    for (int epi = 0; epi < 2; ++epi)
+      BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, epi, m.xp_smem[k], nullptr, nullptr, nullptr, nullptr,
+                          nullptr, 0, s));
   BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)m.sy_smem[0]));
   BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -810,7 +1031,11 @@ int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtens
   p.wpart = ms->wpart.as<float>();
   p.flag = df->ctx->flag;
   const int grid = (int)std::min<int64_t>(m.grid, p.tiles);
-  BQC_TRY(dispatch_xn(m.xn, split, m.xp_smem[k], &p, ms, Ah, Al, grid, s));
+  p.bk = 0;
+  p.q0 = 0;
+  p.bkv = 0;
+  p.naux_ld = 0;
+  BQC_TRY(dispatch_xn(m.xn, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl, grid, s));
   if (w_out) {
     k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
                                                     w_out, ms->w32.as<float>());
@@ -836,6 +1061,9 @@ int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, 
   q.stages = m.sy_stages[k];
   q.part = df->Kpart.as<double>();
   q.flag = df->ctx->flag;
+  q.mode2d = 0;
+  q.kb_total = 0;
+  q.kb_per_chunk = 0;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
   if (split == 3)
     k_syrk_tf32<3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
@@ -874,6 +1102,268 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   df->mark(3, s);
   BQC_TRY(mixed_syrk(df, split, &ms->mapXh, &ms->mapXl, naux, K, s));
   df->mark(4, s);
+  return BQC_OK;
+}
+
+}  // namespace bqc
+
+// ------------------------------------------------- direct mode (mixed) ---
+
+namespace bqc {
+
+// raw (Q|mu nu) of aux rows [qs, qs + nq) of a packed FP64 block -> split
+// shadows laid out [mu][q][ld] (q < bs; rows q >= nq are zero).
+__global__ void k_expand_raw_mu(const double *__restrict__ raw, int64_t npair, int n, int ld,
+                                int bs, int qs, int nq, float *__restrict__ Rh,
+                                float *__restrict__ Rl) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)n * bs * ld;
+  if (e >= tot) return;
+  const int64_t mu = e / ((int64_t)bs * ld), rem = e % ((int64_t)bs * ld);
+  const int q = (int)(rem / ld), nu = (int)(rem % ld);
+  float h = 0.0f, l = 0.0f;
+  if (q < nq && nu < n) {
+    const int64_t hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+    const float f = (float)raw[(int64_t)(qs + q) * npair + hi * (hi + 1) / 2 + lo];
+    h = tf32r(f);
+    l = tf32r(f - h);
+  }
+  Rh[e] = h;
+  if (Rl) Rl[e] = l;
+}
+
+// FP64 L^{-1} (n x n) -> split shadows with rows padded to ld (zeros beyond n).
+__global__ void k_split_f64(const double *__restrict__ a, int n, int ld, float *__restrict__ h,
+                            float *__restrict__ l) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * ld) return;
+  const int64_t r = i / ld, c = i % ld;
+  float hv = 0.0f, lv = 0.0f;
+  if (c < n) {
+    const float f = (float)a[r * n + c];
+    hv = tf32r(f);
+    lv = tf32r(f - hv);
+  }
+  h[i] = hv;
+  l[i] = lv;
+}
+
+struct DirectMixed {
+  MixedPlan plan;      // X-pass / SYRK tile geometry (shared with stored mode)
+  int bs;              // aux rows per X-pass sub-block
+  int ntp;             // P tiles of the TRMM
+  int tr_stages[2];
+  size_t tr_smem[2];
+  int64_t kb_total;    // SYRK k-blocks (ldx * naux_ld / 32)
+  int naux_ld;         // row length of X^T and L^{-1} shadows (Naux rounded to 4: TMA strides)
+  int sy_nchunk;
+  int64_t sy_kbpc;
+  CUtensorMap mapRh, mapRl, mapCh, mapCl, mapXAh, mapXAl, mapLh, mapLl, mapYh, mapYl;
+  DBuf Rh, Rl, Xh, Xl, Lh, Ll, Ch, Cl, Cf, Kpart;
+};
+
+void DirectMixedDeleter::operator()(DirectMixed *p) const { delete p; }
+
+size_t direct_mixed_bytes(int n, int naux, int nocc, int bs) {
+  const MixedPlan m = mixed_plan(n, naux, nocc, 152);
+  size_t b = (size_t)2 * n * bs * m.ld * 4;               // raw shadows of one sub-block
+  const size_t nl = (size_t)round_up(naux, 4);
+  b += (size_t)2 * n * m.ldx * nl * 4;                    // X^T / Y^T hi, lo
+  b += (size_t)2 * naux * nl * 4;                         // L^{-1} hi, lo
+  b += (size_t)3 * m.ldx * m.ld * 4;                      // C split + Cf
+  b += (size_t)m.ntri * std::max(1, 2 * 152 / std::max(1, m.ntri)) * kBM * kBM * 8;
+  return b;
+}
+
+int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s) {
+  const Basis *b = df->basis;
+  const int n = b->nbf, naux = b->naux, no = b->nocc;
+  DirectMixed *dm = new DirectMixed();
+  df->dmixed.reset(dm);
+  dm->plan = mixed_plan(n, naux, no, sm_count());
+  const MixedPlan &m = dm->plan;
+  if (m.xp_stages[1] < 2) return BQC_E_UNSUPPORTED;
+  dm->bs = bs;
+  dm->ntp = (naux + kBM - 1) / kBM;
+  const size_t avail = 232448 - 1024 - 256;
+  for (int k = 0; k < 2; ++k) {
+    const size_t st = (size_t)(k + 1) * 2 * kAStage;
+    dm->tr_stages[k] = (int)std::min<size_t>(8, avail / st);
+    dm->tr_smem[k] = dm->tr_stages[k] * st + 1024 + 256;
+  }
+  dm->naux_ld = round_up(naux, 4);
+  const int nl = dm->naux_ld;
+  dm->kb_total = ((int64_t)m.ldx * nl + 31) / 32;
+  int nch = std::max(1, (2 * m.grid + m.ntri - 1) / m.ntri);
+  nch = (int)std::min<int64_t>(nch, dm->kb_total);
+  dm->sy_kbpc = (dm->kb_total + nch - 1) / nch;
+  dm->sy_nchunk = (int)((dm->kb_total + dm->sy_kbpc - 1) / dm->sy_kbpc);
+  Ctx *ctx = df->ctx;
+  BQC_TRY(dm->Rh.alloc(ctx, (size_t)n * bs * m.ld * 4));
+  BQC_TRY(dm->Rl.alloc(ctx, (size_t)n * bs * m.ld * 4));
+  BQC_TRY(dm->Xh.alloc(ctx, (size_t)n * m.ldx * nl * 4));
+  BQC_TRY(dm->Xl.alloc(ctx, (size_t)n * m.ldx * nl * 4));
+  // padding columns (Q >= Naux) are never written and must read as zero
+  BQC_CUDA_TRY(cudaMemsetAsync(dm->Xh.p, 0, dm->Xh.n, s));
+  BQC_CUDA_TRY(cudaMemsetAsync(dm->Xl.p, 0, dm->Xl.n, s));
+  BQC_TRY(dm->Lh.alloc(ctx, (size_t)naux * nl * 4));
+  BQC_TRY(dm->Ll.alloc(ctx, (size_t)naux * nl * 4));
+  BQC_TRY(dm->Ch.alloc(ctx, (size_t)m.ldx * m.ld * 4));
+  BQC_TRY(dm->Cl.alloc(ctx, (size_t)m.ldx * m.ld * 4));
+  BQC_TRY(dm->Cf.alloc(ctx, (size_t)n * m.ldx * 4));
+  BQC_TRY(dm->Kpart.alloc(ctx, (size_t)dm->sy_nchunk * m.ntri * kBM * kBM * 8));
+  {
+    const int64_t nn = (int64_t)naux * nl;
+    k_split_f64<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Linv, naux, nl, dm->Lh.as<float>(),
+                                                              dm->Ll.as<float>());
+    BQC_LAUNCH_CHECK();
+  }
+  {  // raw sub-block shadows: rows (mu, q), K = nu
+    const uint64_t dims[2] = {(uint64_t)m.ld, (uint64_t)n * bs};
+    const uint64_t str[1] = {(uint64_t)m.ld * 4};
+    const uint32_t box[2] = {32, kBM};
+    BQC_TRY(make_tmap_f32(&dm->mapRh, dm->Rh.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapRl, dm->Rl.p, 2, dims, str, box));
+  }
+  {  // C^T split
+    const uint64_t dims[2] = {(uint64_t)m.ld, (uint64_t)m.ldx};
+    const uint64_t str[1] = {(uint64_t)m.ld * 4};
+    const uint32_t box[2] = {32, (uint32_t)m.xn};
+    BQC_TRY(make_tmap_f32(&dm->mapCh, dm->Ch.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapCl, dm->Cl.p, 2, dims, str, box));
+  }
+  {  // X^T as the TRMM A operand: rows (mu, i), K = Q
+    const uint64_t dims[2] = {(uint64_t)naux, (uint64_t)n * m.ldx};
+    const uint64_t str[1] = {(uint64_t)nl * 4};
+    const uint32_t box[2] = {32, kBM};
+    BQC_TRY(make_tmap_f32(&dm->mapXAh, dm->Xh.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapXAl, dm->Xl.p, 2, dims, str, box));
+  }
+  {  // L^{-1}: rows P, K = Q
+    const uint64_t dims[2] = {(uint64_t)naux, (uint64_t)naux};
+    const uint64_t str[1] = {(uint64_t)nl * 4};
+    const uint32_t box[2] = {32, kBM};
+    BQC_TRY(make_tmap_f32(&dm->mapLh, dm->Lh.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapLl, dm->Ll.p, 2, dims, str, box));
+  }
+  {  // Y^T as the SYRK operand: rows mu, K = (i, P)
+    const uint64_t dims[2] = {(uint64_t)m.ldx * nl, (uint64_t)n};
+    const uint64_t str[1] = {(uint64_t)m.ldx * nl * 4};
+    const uint32_t box[2] = {32, kBM};
+    BQC_TRY(make_tmap_f32(&dm->mapYh, dm->Xh.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapYl, dm->Xl.p, 2, dims, str, box));
+  }
+  for (int k = 0; k < 2; ++k)
+    BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, 1, m.xp_smem[k], nullptr, nullptr, nullptr, nullptr,
+                        nullptr, 0, s));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_trmm_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dm->tr_smem[0]));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_trmm_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dm->tr_smem[1]));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m.sy_smem[0]));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m.sy_smem[1]));
+  return BQC_OK;
+}
+
+int direct_mixed_prep_c(Df *df, const double *C, int split, cudaStream_t s) {
+  DirectMixed *dm = df->dmixed.get();
+  const MixedPlan &m = dm->plan;
+  const int n = df->basis->nbf, no = df->basis->nocc;
+  const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld, (int64_t)n * m.ldx);
+  k_prep_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      C, n, no, m.ld, m.ldx, dm->Ch.as<float>(), split == 3 ? dm->Cl.as<float>() : nullptr,
+      dm->Cf.as<float>());
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+// X^T[mu][i][q0 + q] = sum_nu raw[q][mu nu] C[nu][i] for the nq aux rows of a
+// packed FP64 raw block (in sub-blocks of bs rows).
+int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cudaStream_t s) {
+  DirectMixed *dm = df->dmixed.get();
+  const MixedPlan &m = dm->plan;
+  const int n = df->basis->nbf, naux = df->basis->naux;
+  const int k = split == 3 ? 1 : 0;
+  for (int qs = 0; qs < nq; qs += dm->bs) {
+    const int nv = std::min(dm->bs, nq - qs);
+    const int64_t tot = (int64_t)n * dm->bs * m.ld;
+    k_expand_raw_mu<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        raw, df->npair, n, m.ld, dm->bs, qs, nv, dm->Rh.as<float>(),
+        split == 3 ? dm->Rl.as<float>() : nullptr);
+    BQC_LAUNCH_CHECK();
+    XpassParams p;
+    p.rows = (int64_t)n * dm->bs;
+    p.n = n;
+    p.ldx = m.ldx;
+    p.ncg = m.ncg;
+    p.kblocks = (m.ld + 31) / 32;
+    p.stages = m.xp_stages[k];
+    p.tiles = (p.rows + kBM - 1) / kBM * m.ncg;
+    p.Xh = dm->Xh.as<float>();
+    p.Xl = dm->Xl.as<float>();
+    p.Cf = dm->Cf.as<float>();
+    p.wpart = nullptr;
+    p.flag = df->ctx->flag;
+    p.bk = dm->bs;
+    p.q0 = q0 + qs;
+    p.bkv = nv;
+    p.naux_ld = dm->naux_ld;
+    const int grid = (int)std::min<int64_t>(m.grid, p.tiles);
+    BQC_TRY(dispatch_xn(m.xn, split, 1, m.xp_smem[k], &p, &dm->mapRh, &dm->mapRl, &dm->mapCh,
+                        &dm->mapCl, grid, s));
+  }
+  return BQC_OK;
+}
+
+// After all blocks: Y = L^{-1} X in place on X^T, then K = sum_{P,i} Y Y^T.
+int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
+  DirectMixed *dm = df->dmixed.get();
+  const MixedPlan &m = dm->plan;
+  const int n = df->basis->nbf, naux = df->basis->naux;
+  const int k = split == 3 ? 1 : 0;
+  TrmmParams t;
+  t.rows = (int64_t)n * m.ldx;
+  t.naux = naux;
+  t.ld = dm->naux_ld;
+  t.ntp = dm->ntp;
+  t.stages = dm->tr_stages[k];
+  t.mtiles = (t.rows + kBM - 1) / kBM;
+  t.Xh = dm->Xh.as<float>();
+  t.Xl = dm->Xl.as<float>();
+  t.flag = df->ctx->flag;
+  const int tg = (int)std::min<int64_t>(m.grid, t.mtiles);
+  if (split == 3)
+    k_trmm_tf32<3><<<tg, kThreads, dm->tr_smem[1], s>>>(dm->mapXAh, dm->mapXAl, dm->mapLh,
+                                                        dm->mapLl, t);
+  else
+    k_trmm_tf32<1><<<tg, kThreads, dm->tr_smem[0], s>>>(dm->mapXAh, dm->mapXAh, dm->mapLh,
+                                                        dm->mapLh, t);
+  BQC_LAUNCH_CHECK();
+  SyrkParams q;
+  q.n = n;
+  q.ldx = m.ldx;
+  q.naux = naux;
+  q.ntri = m.ntri;
+  q.nchunk = dm->sy_nchunk;
+  q.p_per_chunk = 0;
+  q.nib = m.ldx / 32;
+  q.stages = m.sy_stages[k];
+  q.part = dm->Kpart.as<double>();
+  q.flag = df->ctx->flag;
+  q.mode2d = 1;
+  q.kb_total = dm->kb_total;
+  q.kb_per_chunk = dm->sy_kbpc;
+  const int grid = std::min(m.grid, q.ntri * q.nchunk);
+  if (split == 3)
+    k_syrk_tf32<3><<<grid, kThreads, m.sy_smem[1], s>>>(dm->mapYh, dm->mapYl, q);
+  else
+    k_syrk_tf32<1><<<grid, kThreads, m.sy_smem[0], s>>>(dm->mapYh, dm->mapYh, q);
+  BQC_LAUNCH_CHECK();
+  k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(dm->Kpart.as<double>(),
+                                                                  q.nchunk, m.ntri, n, K);
+  BQC_LAUNCH_CHECK();
   return BQC_OK;
 }
 
