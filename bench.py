@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-precs", default="mixed_tf32x3,fp64")
     ap.add_argument("--direct", action="store_true",
                     help="direct (on-the-fly) DF run, default (H2O)_128")
     return ap.parse_args()
@@ -191,7 +192,9 @@ def run_serve(args):
     ctx = bqc.Context(0)
     stream = workload.serving_stream(nreq=args.serve_requests, rate_hz=args.serve_rate)
     out = {}
-    for prec, label in ((bqc.PREC_MIXED_TF32X3, "mixed_tf32x3"), (bqc.PREC_FP64, "fp64")):
+    precs = {"mixed_tf32x3": bqc.PREC_MIXED_TF32X3, "fp64": bqc.PREC_FP64}
+    for label in args.serve_precs.split(","):
+        prec = precs[label]
         srv = bqc.Server(ctx, max_slots=args.serve_slots, hbm_budget=150 * 10 ** 9, prec=prec)
         clocks = ClockSampler(gpu_index(0))
         clocks.start()
@@ -203,7 +206,18 @@ def run_serve(args):
                 time.sleep(ta - now)
             mol = workload.water_cluster(n, seed=rid)
             tickets.append((ta, n, srv.submit(mol)))
-        srv.drain(0)
+        done = set()
+        while len(done) < len(tickets):
+            for (ta, n, t) in tickets:
+                if t in done:
+                    continue
+                r = srv.poll(t)
+                if r is not None:
+                    done.add(t)
+                    print(f"[serve {label}] n={n} nbf={r['nbf']} status={r['status']} "
+                          f"iters={r['iterations']} wait={r['t_admit'] - r['t_submit']:.2f}s "
+                          f"run={r['t_done'] - r['t_admit']:.2f}s", file=sys.stderr, flush=True)
+            time.sleep(0.05)
         wall = time.perf_counter() - t0
         clk = clocks.stop()
         lat, ok, nbf = [], 0, []

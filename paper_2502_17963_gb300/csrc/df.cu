@@ -271,12 +271,17 @@ int bqc_df_phase_ms(bqc_df *df, float *ms, int n) {
   if (!df || !ms || n <= 0) return BQC_E_INVALID;
   if (!df->timed) return BQC_E_NOT_READY;
   BQC_CUDA_TRY(cudaEventSynchronize(df->ev[4]));
-  float t[4] = {0, 0, 0, 0}, a = 0, b = 0;
+  float t[4] = {0, 0, 0, 0};
   BQC_CUDA_TRY(cudaEventElapsedTime(&t[0], df->ev[1], df->ev[2]));
-  BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[3]));
-  BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[3], df->ev[4]));
-  BQC_CUDA_TRY(cudaEventElapsedTime(&a, df->ev[0], df->ev[1]));
-  t[3] = a + b;
+  BQC_CUDA_TRY(cudaEventElapsedTime(&t[3], df->ev[0], df->ev[1]));
+  if (df->mode == BQC_DF_STORED && df->side && df->last_mixed) {
+    // mixed stored build: J pass (side stream, ev2 -> ev5) overlaps the SYRK (ev2 -> ev3)
+    BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[5]));
+    BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[2], df->ev[3]));
+  } else {
+    BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[3]));
+    BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[3], df->ev[4]));
+  }
   for (int i = 0; i < n && i < 4; ++i) ms[i] = t[i];
   return BQC_OK;
 }
@@ -287,6 +292,7 @@ int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K
   if (nocc != df->basis->nocc) return BQC_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   if (df->timing) df->timed = true;
+  df->last_mixed = prec != BQC_PREC_FP64;
   if (df->mode == BQC_DF_DIRECT) return jk_direct(df, C, prec, J, K, s);
   if (prec == BQC_PREC_FP64) return jk_fp64_stored(df, C, J, K, s);
   if (prec == BQC_PREC_MIXED_TF32 || prec == BQC_PREC_MIXED_TF32X3) {

@@ -47,14 +47,20 @@ struct Df {
   int aux_block = 1024;
   std::unique_ptr<DirectMixed, DirectMixedDeleter> dmixed;  // tensor-core state
   // phase timing (bqc_df_timing)
-  bool timing = false, timed = false;
+  bool timing = false, timed = false, last_mixed = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void mark(int i, cudaStream_t s) {
     if (timing && ev[i]) cudaEventRecord(ev[i], s);
   }
+  // side stream of the mixed build: the J pass runs there concurrently with the SYRK
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   ~Df() {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
   size_t device_bytes() const {
     return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +

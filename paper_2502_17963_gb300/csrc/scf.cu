@@ -109,14 +109,35 @@ static bool diis_solve(const std::vector<double> &Bm, int m, std::vector<double>
   return true;
 }
 
+// cuBLAS / cuSOLVER handles cached per host thread and device: creating a
+// handle allocates device memory, which synchronises the device and would
+// serialise concurrent solves (serving slots run one thread each).
 struct ScfWork {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t sol = nullptr;
-  ~ScfWork() {
-    if (blas) cublasDestroy(blas);
-    if (sol) cusolverDnDestroy(sol);
-  }
 };
+
+struct HandleCache {
+  int device = -1;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t sol = nullptr;
+};
+
+static int get_handles(int device, ScfWork &w) {
+  static thread_local HandleCache hc;
+  if (hc.device != device) {
+    if (hc.blas) cublasDestroy(hc.blas);
+    if (hc.sol) cusolverDnDestroy(hc.sol);
+    hc.blas = nullptr;
+    hc.sol = nullptr;
+    BQC_BLAS_TRY(cublasCreate(&hc.blas));
+    BQC_SOLVER_TRY(cusolverDnCreate(&hc.sol));
+    hc.device = device;
+  }
+  w.blas = hc.blas;
+  w.sol = hc.sol;
+  return BQC_OK;
+}
 
 // Symmetric eigen-decomposition in place (columns of A become eigenvectors).
 static int eigh(ScfWork &w, Ctx *ctx, double *A, int n, double *evals, DBuf &work, DBuf &info,
@@ -143,11 +164,10 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   const int n = b->nbf, no = b->nocc;
   const int64_t nn = (int64_t)n * n;
   ScfWork w;
-  BQC_BLAS_TRY(cublasCreate(&w.blas));
+  BQC_TRY(get_handles(ctx->device, w));
   BQC_BLAS_TRY(cublasSetStream(w.blas, s));
   BQC_BLAS_TRY(cublasSetPointerMode(w.blas, CUBLAS_POINTER_MODE_HOST));
   BQC_BLAS_TRY(cublasSetMathMode(w.blas, CUBLAS_PEDANTIC_MATH));
-  BQC_SOLVER_TRY(cusolverDnCreate(&w.sol));
   BQC_SOLVER_TRY(cusolverDnSetStream(w.sol, s));
   DBuf S, T, V, H, F, J, K, D, X, U, ev, Cc, Fp, t1, t2, Crm, work, info, Fx;
   for (DBuf *p : {&S, &T, &V, &H, &F, &J, &K, &D, &X, &U, &Cc, &Fp, &t1, &t2, &Fx})
@@ -199,14 +219,54 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   double E = 0.0, Eprev = 0.0, emax = INFINITY;
   bool have_prev = false, converged = false;
   int it = 0;
-  for (it = 1; it <= o.max_iter; ++it) {
+  // The Fock build of an iteration (C -> C_occ row-major, J, K, F) has no
+  // host synchronisation in stored mode, so it is captured once per precision
+  // stage into a CUDA graph and replayed (thread-local capture mode: other
+  // threads, e.g. other serving slots, keep launching meanwhile).
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  auto fock_build = [&](int prec) -> int {
     k_cm_to_rm<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, Cc.as<double>(), n, Crm.as<double>());
     BQC_LAUNCH_CHECK();
-    BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Crm.as<double>(), no, stage, J.as<double>(),
+    BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Crm.as<double>(), no, prec, J.as<double>(),
                    K.as<double>(), (bqc_stream_t)s));
     k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, J.as<double>(), 2.0,
                                       K.as<double>(), -1.0, F.as<double>());
     BQC_LAUNCH_CHECK();
+    return BQC_OK;
+  };
+  const bool use_graph = df->mode == BQC_DF_STORED && !df->timing && s != nullptr;
+  auto graph_free = [&]() {
+    for (auto &g : gexec)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+  };
+  for (it = 1; it <= o.max_iter; ++it) {
+    if (use_graph && stage >= 0 && stage < 3) {
+      if (!gexec[stage]) {
+        cudaGraph_t graph = nullptr;
+        BQC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int st = fock_build(stage);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != BQC_OK || ce != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          graph_free();
+          if (st != BQC_OK) return st;
+          BQC_CUDA_TRY(ce);
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&gexec[stage], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+          graph_free();
+          BQC_CUDA_TRY(ie);
+        }
+      }
+      const cudaError_t le = cudaGraphLaunch(gexec[stage], s);
+      if (le != cudaSuccess) {
+        graph_free();
+        BQC_CUDA_TRY(le);
+      }
+    } else {
+      BQC_TRY(fock_build(stage));
+    }
     BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, no, &one, Cc.as<double>(), n,
                              Cc.as<double>(), n, &zero, D.as<double>(), n));
     k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, F.as<double>(), 1.0, nullptr, 0.0,
@@ -308,6 +368,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     }
     BQC_TRY(diag(Fuse));
   }
+  graph_free();
   if (it > o.max_iter) it = o.max_iter;
   // results (library-owned buffers, row-major C)
   res->energy = E;

@@ -734,17 +734,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Block b owns rows b and N-1-b (balanced work); a thread owns 4 consecutive
 // columns of one row and streams every P (float4 loads, FP32 partial sums
 // over 64 P, folded into FP64).
+// Blocks are small (kJThreads) so that one fits beside a persistent SYRK CTA
+// on each SM: the J pass streams HBM while the SYRK keeps the tensor cores busy.
+constexpr int kJThreads = 128;
+
 template <int SPLIT>
-__global__ void __launch_bounds__(512) k_jpass_tf32(const float *__restrict__ Bh,
-                                                    const float *__restrict__ Bl,
-                                                    const float *__restrict__ w32, int naux, int n,
-                                                    int ld, double *__restrict__ Jp) {
+__global__ void __launch_bounds__(kJThreads) k_jpass_tf32(const float *__restrict__ Bh,
+                                                          const float *__restrict__ Bl,
+                                                          const float *__restrict__ w32, int naux,
+                                                          int n, int ld, double *__restrict__ Jp) {
   const int b = blockIdx.x;
   const int r1 = b, r2 = n - 1 - b;
   const int c1 = r1 / 4 + 1;
   const int c2 = (r2 != r1) ? r2 / 4 + 1 : 0;
   const int64_t nn = (int64_t)n * ld;
-  for (int it = threadIdx.x; it < c1 + c2; it += blockDim.x) {
+  for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < c1 + c2;
+       it += gridDim.y * blockDim.x) {
     const int row = it < c1 ? r1 : r2;
     const int q = it < c1 ? it : it - c1;
     const int64_t off = (int64_t)row * ld + 4 * q;
@@ -950,6 +955,11 @@ int mixed_setup(Df *df, cudaStream_t s) {
   ms->plan = mixed_plan(n, naux, no, sm_count());
   const MixedPlan &m = ms->plan;
   if (m.xp_stages[1] < 2 || m.sy_stages[1] < 2) return BQC_E_UNSUPPORTED;
+  if (!df->side) {
+    BQC_CUDA_TRY(cudaStreamCreateWithFlags(&df->side, cudaStreamNonBlocking));
+    BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork, cudaEventDisableTiming));
+    BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
+  }
   Ctx *ctx = df->ctx;
   // split shadow of B (Bh lives in df->B32, allocated by the caller)
   BQC_TRY(ms->Bl.alloc(ctx, (size_t)naux * n * m.ld * 4));
@@ -1087,20 +1097,31 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   BQC_TRY(mixed_xpass(df, C, split, s, &ms->mapAh, &ms->mapAl, rows, df->X32.as<float>(),
                       ms->Xl.as<float>(), df->w.as<double>()));
   df->mark(2, s);
-  // J pass (HBM-bound) over the lower triangle of the B shadow
-  const int threads = std::min(512, round_up((n - 1) / 4 + 3, 32));
+  // J pass (HBM-bound) on the side stream, concurrent with the SYRK
+  cudaStream_t js = s;
+  if (df->side) {
+    BQC_CUDA_TRY(cudaEventRecord(df->fork, s));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(df->side, df->fork, 0));
+    js = df->side;
+  }
+  const dim3 jgrid((unsigned)((n + 1) / 2), (unsigned)(((n - 1) / 4 + 2 + kJThreads - 1) / kJThreads));
   if (split == 3)
-    k_jpass_tf32<3><<<(unsigned)((n + 1) / 2), threads, 0, s>>>(
-        df->B32.as<float>(), ms->Bl.as<float>(), ms->w32.as<float>(), naux, n, m.ld,
-        df->Jp.as<double>());
+    k_jpass_tf32<3><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), ms->Bl.as<float>(),
+                                                 ms->w32.as<float>(), naux, n, m.ld,
+                                                 df->Jp.as<double>());
   else
-    k_jpass_tf32<1><<<(unsigned)((n + 1) / 2), threads, 0, s>>>(
-        df->B32.as<float>(), nullptr, ms->w32.as<float>(), naux, n, m.ld, df->Jp.as<double>());
+    k_jpass_tf32<1><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), nullptr, ms->w32.as<float>(),
+                                                 naux, n, m.ld, df->Jp.as<double>());
   BQC_LAUNCH_CHECK();
-  k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(), n, J);
+  k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, js>>>(df->Jp.as<double>(), n, J);
   BQC_LAUNCH_CHECK();
-  df->mark(3, s);
+  if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
   BQC_TRY(mixed_syrk(df, split, &ms->mapXh, &ms->mapXl, naux, K, s));
+  df->mark(3, s);
+  if (df->side) {
+    BQC_CUDA_TRY(cudaEventRecord(df->join, df->side));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->join, 0));
+  }
   df->mark(4, s);
   return BQC_OK;
 }
