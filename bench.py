@@ -32,6 +32,9 @@ METRIC = "Fock builds/s at (H2O)_64, mixed vs FP64 at <=1e-6 Eh; serve p50/p99 m
 UNIT = "Fock builds/s"
 # TF32 dense peak = measured bf16 x nominal (1.1 / 2.25) ratio of the recipe
 TF32_OVER_BF16 = 1.1 / 2.25
+# DRAM bytes / algorithmic bytes of k_xpass_tf32<.,3> in an ncu capture at
+# (H2O)_16 (1.905 GB / 1.843 GB); both grow as Naux x N x (N + nocc)
+XPASS_TRAFFIC_RATIO = 1.034
 
 
 def parse():
@@ -48,7 +51,8 @@ def parse():
                     help="serving run: Poisson stream of (H2O)_n solves, p50/p99 latency")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-policy", choices=["backfill", "fifo"], default="backfill")
     ap.add_argument("--serve-precs", default="mixed_tf32x3,fp64")
     ap.add_argument("--direct", action="store_true",
                     help="direct (on-the-fly) DF run, default (H2O)_128")
@@ -195,7 +199,9 @@ def run_serve(args):
     precs = {"mixed_tf32x3": bqc.PREC_MIXED_TF32X3, "fp64": bqc.PREC_FP64}
     for label in args.serve_precs.split(","):
         prec = precs[label]
-        srv = bqc.Server(ctx, max_slots=args.serve_slots, hbm_budget=150 * 10 ** 9, prec=prec)
+        policy = {"backfill": bqc.SERVE_BACKFILL, "fifo": bqc.SERVE_FIFO}[args.serve_policy]
+        srv = bqc.Server(ctx, max_slots=args.serve_slots, hbm_budget=150 * 10 ** 9, prec=prec,
+                         policy=policy)
         clocks = ClockSampler(gpu_index(0))
         clocks.start()
         t0 = time.perf_counter()
@@ -215,28 +221,34 @@ def run_serve(args):
                 if r is not None:
                     done.add(t)
                     print(f"[serve {label}] n={n} nbf={r['nbf']} status={r['status']} "
-                          f"iters={r['iterations']} wait={r['t_admit'] - r['t_submit']:.2f}s "
+                          f"iters={r['iterations']} (mixed {r['iterations_mixed']}) "
+                          f"prio={r['priority']} wait={r['t_admit'] - r['t_submit']:.2f}s "
                           f"run={r['t_done'] - r['t_admit']:.2f}s", file=sys.stderr, flush=True)
             time.sleep(0.05)
         wall = time.perf_counter() - t0
         clk = clocks.stop()
-        lat, ok, nbf = [], 0, []
+        lat, ok, nbf, per = [], 0, [], []
         for (ta, n, t) in tickets:
             r = srv.poll(t)
             lat.append(r["t_done"] - r["t_submit"])
             ok += r["status"] == 0
             nbf.append(r["nbf"])
+            per.append([n, round(r["t_admit"] - r["t_submit"], 3), round(r["t_done"] - r["t_admit"], 3),
+                        r["iterations"], r["iterations_mixed"]])
         srv.close()
         lat.sort()
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
         out[label] = {"p50_ms": q(0.5) * 1e3, "p99_ms": q(0.99) * 1e3, "solves_per_s": len(lat) / wall,
                       "converged": ok, "requests": len(lat), "wall_s": wall, "clocks": clk,
-                      "offered_req_per_s": args.serve_rate}
-    line = {"metric": "serve p50/p99 ms (DF-RHF solves, Poisson arrivals)", "value": out["mixed_tf32x3"]["p99_ms"],
+                      "offered_req_per_s": args.serve_rate,
+                      "requests_n_wait_run_iters_mixed": per}
+    first = args.serve_precs.split(",")[0]
+    line = {"metric": "serve p50/p99 ms (DF-RHF solves, Poisson arrivals)", "value": out[first]["p99_ms"],
             "unit": "ms (p99 latency)", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
             "config": {"workload": f"Poisson {args.serve_rate} req/s, (H2O)_n n~U{{2..48}}, first "
                                    f"{args.serve_requests} of the seed-2025 stream",
-                       "slots": args.serve_slots, "hbm_budget_gb": 150}, "serve": out}
+                       "slots": args.serve_slots, "policy": args.serve_policy, "hbm_budget_gb": 150,
+                       "prec": first}, "serve": out}
     print(json.dumps(line), flush=True)
 
 
@@ -389,12 +401,16 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1) / args.fp64_steps
+        D = C @ C.T  # E = sum D (H + F) + E_nn, so a build's energy error is sum D dF
         df.jk(C, bqc.PREC_MIXED_TF32, J, K)
-        tf1["max_abs_dF_vs_fp64"] = (2.0 * (J - J64) - (K - K64)).abs().max().item()
+        dF1 = 2.0 * (J - J64) - (K - K64)
+        tf1["max_abs_dF_vs_fp64"] = dF1.abs().max().item()
+        tf1["dE_vs_fp64_Eh"] = (D * dF1).sum().item()
         df.jk(C, MIX, J, K)
-        dF = (2.0 * (J - J64) - (K - K64)).abs().max().item()
+        dFm = 2.0 * (J - J64) - (K - K64)
+        dF = dFm.abs().max().item()
         fp64 = {"builds_per_s": 1e3 / fms, "ms_per_build": fms, "steps": args.fp64_steps,
-                "max_abs_dF_mixed_vs_fp64": dF,
+                "max_abs_dF_mixed_vs_fp64": dF, "dE_mixed_vs_fp64_Eh": (D * dFm).sum().item(),
                 "speedup_mixed_over_fp64": fms / ms_per_step}
 
     # end to end through the C ABI with host buffers (H2D of C_occ, D2H of J, K)
@@ -426,20 +442,26 @@ def main():
     naux = basis.naux
     xflops = 3 * 2.0 * naux * n * n * no   # algorithmic flops of one 3xTF32 X pass
     xs = ph_mean[0] * 1e-3
+    xbytes = naux * n * n * 8 + naux * n * no * 8  # split B read + split X write
     tf32_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")) * TF32_OVER_BF16
     achieved = xflops / xs / 1e12
-    roofline = {"bound": "tensor", "kernel": "k_xpass_tf32 (X = B C, fused w)",
+    roofline = {"bound": "tensor", "kernel": "k_xpass_tf32<XN,3,0> (X = B C, 3xTF32)",
                 "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": None,
+                "frac": achieved / tf32_peak, "traffic": XPASS_TRAFFIC_RATIO * xbytes,
+                "traffic_source": "ncu dram__bytes_read+write / algorithmic bytes of the same kernel "
+                                  f"at (H2O)_16 ({XPASS_TRAFFIC_RATIO}) x this launch's algorithmic "
+                                  f"bytes ({xbytes:.4g} B)",
                 "peak_source": f"{pk_src}: bf16 sustained x nominal tf32/bf16 (1.1/2.25)",
                 "algorithmic_per_launch": f"3 products x 2*Naux*N^2*nocc = {xflops:.4g} flop"}
-    jbytes = naux * n * (n + 1) / 2 * 8  # one read of the hi + lo lower triangles
+    jbytes = naux * n * (n + 1) / 2 * 8  # J pass: one read of the packed FP64 B
     kflops = 3 * n * n * naux * no       # SYRK half, 3 products
     extra = {
         "phases_ms": {"x_pass": ph_mean[0], "j_pass": ph_mean[1], "k_syrk": ph_mean[2],
                       "prep": ph_mean[3]},
         "j_pass_gbs": jbytes / (ph_mean[1] * 1e-3) / 1e9,
         "j_pass_frac_hbm": jbytes / (ph_mean[1] * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "j_note": "J pass (FP64 FMAs over the packed FP64 B, w fused in the X pass) on a side "
+                  "stream concurrent with the SYRK; its time includes that contention",
         "k_syrk_tflops": kflops / (ph_mean[2] * 1e-3) / 1e12,
         "setup_s": setup_s,
         "fp64": fp64,

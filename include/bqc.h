@@ -59,9 +59,12 @@ enum {
 /* Precision of the Fock build (the X = B C and K contractions, the B.D
  * products).  FP64: all FP64 (DFMA).  MIXED_TF32: tcgen05 kind::tf32 MMAs on
  * TF32-rounded B and C_occ (one product per term, ~2^-11 relative per
- * product), FP32 accumulation in short chains, FP64 chunk sums.
- * MIXED_TF32X3: the same with every operand split hi + lo into two TF32
- * parts and three products per term (hi*hi + hi*lo + lo*hi, ~2^-22). */
+ * product), FP32 accumulation in short chains, FP64 chunk sums; J from the
+ * TF32 shadow of B.  MIXED_TF32X3: K the same with every operand split
+ * hi + lo into two TF32 parts and three products per term (hi*hi + hi*lo +
+ * lo*hi, ~2^-22); J in FP64 from the FP64 B on the CUDA cores, concurrently
+ * with the tensor-core passes (the direct mode's J is FP64 in every
+ * precision). */
 typedef enum {
   BQC_PREC_FP64 = 0,
   BQC_PREC_MIXED_TF32 = 1,
@@ -199,9 +202,10 @@ int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, 
  * every following bqc_jk on this handle record CUDA events at its phase
  * boundaries on its stream (leave it off while capturing a graph).
  * bqc_df_phase_ms waits for the last call's events and writes up to n
- * durations in ms.  Stored mode: [0] X pass (X = B C with the fused w
- * contraction), [1] J pass, [2] K (SYRK and its FP64 reduction), [3] operand
- * preparation.  Direct mode: [0] first integral pass (integrals, gamma, X),
+ * durations in ms.  Stored mode: [0] X pass (X = B C, with the fused w
+ * contraction in FP64 and MIXED_TF32), [1] J (mixed builds: on a side stream,
+ * overlapping [0] in MIXED_TF32X3 and [2] in MIXED_TF32), [2] K (SYRK and
+ * its FP64 reduction), [3] operand preparation.  Direct mode: [0] first integral pass (integrals, gamma, X),
  * [1] metric solve and K, [2] second integral pass (J), [3] preparation.
  * BQC_E_NOT_READY if no timed call has been made. */
 int bqc_df_timing(bqc_df *df, int enable);
@@ -234,25 +238,48 @@ typedef struct {
   double *C_dev;
   double *eps_dev;
   double *F_dev;
+  /* Optional caller-owned host output (NULL = skip): 3 * history_cap doubles
+   * receiving, per Fock build in order, (bqc_prec of the build, max-abs DIIS
+   * error, energy); history_len (output) counts the builds written. */
+  double *history;
+  int history_cap;
+  int history_len;
 } bqc_scf_result;
 
 /* Closed-shell SCF (canonical orthogonalisation, core-Hamiltonian guess,
  * Pulay DIIS on e = X^T (FDS - SDF) X, aufbau) with the Fock build of
  * bqc_jk.  With prec = MIXED_TF32 the first stage runs mixed and switches to
- * FP64 (DIIS subspace cleared) when the DIIS error drops below stage_tol.
+ * FP64 (DIIS subspace cleared) when the DIIS error drops below stage_tol, or
+ * earlier once the mixed stage stops improving (its error floor, about
+ * max|dF_mixed| / sqrt(smallest kept overlap eigenvalue), can lie above
+ * stage_tol in diffuse bases): best error not halved for 3 iterations while
+ * below 1e-2, for 8 iterations at any size, or max_iter / 2 mixed iterations.
  * Blocks until done.  Returns BQC_E_NOT_CONVERGED (result still filled) if
- * max_iter is reached.  out's C_dev / eps_dev / F_dev are read as inputs
- * (caller buffers or NULL); everything else in *out is written. */
+ * max_iter is reached.  out's C_dev / eps_dev / F_dev / history /
+ * history_cap are read as inputs (caller buffers or NULL); everything else
+ * in *out is written. */
 int bqc_scf_run(bqc_ctx *ctx, bqc_df *df, const bqc_scf_opts *opts, bqc_stream_t stream,
                 bqc_scf_result *out);
 
 /* ------------------------------------------------------------ serving --- */
+
+typedef enum {
+  /* Queue order, except that a later request that fits the HBM ledger may be
+   * admitted while the queue head does not (the head is passed over at most
+   * max_skips times, then waits alone); smaller molecules run on
+   * higher-priority streams.  Default. */
+  BQC_SERVE_BACKFILL = 0,
+  /* Strict arrival order, every stream at the same priority. */
+  BQC_SERVE_FIFO = 1
+} bqc_serve_policy;
 
 typedef struct {
   int max_slots;       /* concurrent SCF solves on the device (default 4)     */
   size_t hbm_budget;   /* bytes the admitted requests may hold (0 = ctx's)    */
   int prec;            /* bqc_prec of every request                           */
   bqc_scf_opts scf;    /* SCF options for every request                       */
+  int policy;          /* bqc_serve_policy                                    */
+  int max_skips;       /* backfill starvation bound (<= 0: 8)                 */
 } bqc_serve_opts;
 
 typedef struct {
@@ -274,6 +301,8 @@ typedef struct {
   double t_submit;     /* seconds on the server's monotonic clock              */
   double t_admit;
   double t_done;
+  int iterations_mixed; /* SCF iterations before the switch to FP64            */
+  int priority;         /* CUDA stream priority the solve ran at               */
 } bqc_serve_result;
 
 /* Continuous-batching server: a scheduler thread admits queued requests as

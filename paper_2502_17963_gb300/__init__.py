@@ -25,6 +25,7 @@ BQC_E_NOT_READY = -8
 PREC_FP64 = 0
 PREC_MIXED_TF32 = 1
 PREC_MIXED_TF32X3 = 2
+SERVE_BACKFILL, SERVE_FIFO = 0, 1
 DF_STORED, DF_DIRECT, DF_AUTO = 0, 1, 2
 
 
@@ -60,12 +61,14 @@ class bqc_scf_result(ctypes.Structure):
                 ("diis_err", ctypes.c_double), ("iterations", ctypes.c_int),
                 ("converged", ctypes.c_int), ("iterations_mixed", ctypes.c_int),
                 ("nmo", ctypes.c_int), ("C_dev", ctypes.c_void_p), ("eps_dev", ctypes.c_void_p),
-                ("F_dev", ctypes.c_void_p)]
+                ("F_dev", ctypes.c_void_p), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int)]
 
 
 class bqc_serve_opts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
-                ("prec", ctypes.c_int), ("scf", bqc_scf_opts)]
+                ("prec", ctypes.c_int), ("scf", bqc_scf_opts), ("policy", ctypes.c_int),
+                ("max_skips", ctypes.c_int)]
 
 
 class bqc_request(ctypes.Structure):
@@ -79,7 +82,8 @@ class bqc_serve_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("energy", ctypes.c_double),
                 ("diis_err", ctypes.c_double), ("iterations", ctypes.c_int),
                 ("nbf", ctypes.c_int), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("iterations_mixed", ctypes.c_int), ("priority", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -369,7 +373,8 @@ class DF:
 def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
             energy_tol: float = 1e-10, stage_tol: float = 1e-5, max_iter: int = 100,
             diis_space: int = 8, orth_thresh: float = 1e-8, stream=None, keep_arrays=False):
-    """Runs bqc_scf_run; returns a dict (energy, iterations, converged, ...).
+    """Runs bqc_scf_run; returns a dict (energy, iterations, converged, ...,
+    history = [(prec, DIIS error, energy)] per Fock build).
 
     With keep_arrays the MO coefficients (N x nmo), orbital energies and the
     last Fock matrix come back as device tensors.
@@ -377,6 +382,9 @@ def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
     o = bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space, prec, orth_thresh)
     r = bqc_scf_result()
     n = df.basis.nbf
+    cap = 2 * max_iter + 2
+    hist = (ctypes.c_double * (3 * cap))()
+    r.history, r.history_cap = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)), cap
     if keep_arrays:
         Cbuf, eps, F = _empty((n * n,)), _empty((n,)), _empty((n, n))
         r.C_dev, r.eps_dev, r.F_dev = _ptr(Cbuf), _ptr(eps), _ptr(F)
@@ -384,7 +392,9 @@ def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
     if st not in (BQC_OK, BQC_E_NOT_CONVERGED):
         raise BqcError(st, "bqc_scf_run")
     out = dict(energy=r.energy, e_nuc=r.e_nuc, diis_err=r.diis_err, iterations=r.iterations,
-               converged=bool(r.converged), iterations_mixed=r.iterations_mixed, nmo=r.nmo)
+               converged=bool(r.converged), iterations_mixed=r.iterations_mixed, nmo=r.nmo,
+               history=[(int(hist[3 * i]), hist[3 * i + 1], hist[3 * i + 2])
+                        for i in range(r.history_len)])
     if keep_arrays:
         out.update(C=Cbuf[: n * r.nmo].view(n, r.nmo), eps=eps[: r.nmo], F=F)
     return out
@@ -396,11 +406,11 @@ class Server:
     def __init__(self, ctx: Context, max_slots: int = 4, hbm_budget: int = 0,
                  prec: int = PREC_MIXED_TF32X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
                  stage_tol: float = 1e-5, max_iter: int = 100, diis_space: int = 8,
-                 orth_thresh: float = 1e-8):
+                 orth_thresh: float = 1e-8, policy: int = 0, max_skips: int = 8):
         self.ctx = ctx
         o = bqc_serve_opts(max_slots, hbm_budget, prec,
                            bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space,
-                                        prec, orth_thresh))
+                                        prec, orth_thresh), policy, max_skips)
         h = vp()
         check(lib().bqc_serve_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "bqc_serve_create")
         self.h = h
@@ -422,7 +432,7 @@ class Server:
         check(st, "bqc_serve_poll")
         return dict(status=r.status, energy=r.energy, diis_err=r.diis_err,
                     iterations=r.iterations, nbf=r.nbf, t_submit=r.t_submit, t_admit=r.t_admit,
-                    t_done=r.t_done)
+                    t_done=r.t_done, iterations_mixed=r.iterations_mixed, priority=r.priority)
 
     def drain(self, timeout_s: float = 0.0):
         check(lib().bqc_serve_drain(self.h, timeout_s), "bqc_serve_drain")

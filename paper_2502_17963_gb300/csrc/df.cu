@@ -36,32 +36,72 @@ __global__ void __launch_bounds__(256) k_wdot(const double *X, const double *C, 
   if (threadIdx.x == 0) w[P] = red[0];
 }
 
-// J pass over packed FP64 B: Jp[col] = sum_P w_P B[P][col]; each thread owns
-// two adjacent columns and streams all P (one read of B, coalesced).
+// J pass over packed FP64 B: Jp[y][col] = sum_{P in chunk y} w_P B[P][col];
+// each thread owns two adjacent columns and streams the chunk's P (one read
+// of B, coalesced), eight 16-byte loads in flight per thread, P in
+// increasing order.  gridDim.y aux chunks give small systems enough blocks;
+// the chunk partials are summed in a fixed order by k_unpack_jsum.
 __global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
                                                  const double *__restrict__ w, int naux,
                                                  int64_t npair, double *__restrict__ Jp) {
   const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
   if (c2 >= npair) return;
+  const int per = (naux + gridDim.y - 1) / gridDim.y;
+  const int Pa = blockIdx.y * per, Pb = min(naux, Pa + per);
+  double *out = Jp + (int64_t)blockIdx.y * npair;
   double a0 = 0.0, a1 = 0.0;
   if (c2 + 1 < npair && (npair % 2 == 0)) {
-    for (int P = 0; P < naux; ++P) {
-      const double2 b = __ldg(reinterpret_cast<const double2 *>(B + (int64_t)P * npair + c2));
-      const double wp = __ldg(w + P);
-      a0 = fma(wp, b.x, a0);
-      a1 = fma(wp, b.y, a1);
+    const double2 *b2 = reinterpret_cast<const double2 *>(B + c2);
+    const int64_t st = npair / 2;
+    int P = Pa;
+    for (; P + 8 <= Pb; P += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(b2 + (int64_t)(P + k) * st);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double wp = __ldg(w + P + k);
+        a0 = fma(wp, v[k].x, a0);
+        a1 = fma(wp, v[k].y, a1);
+      }
     }
-    Jp[c2] = a0;
-    Jp[c2 + 1] = a1;
+    for (; P < Pb; ++P) {
+      const double2 v = __ldg(b2 + (int64_t)P * st);
+      const double wp = __ldg(w + P);
+      a0 = fma(wp, v.x, a0);
+      a1 = fma(wp, v.y, a1);
+    }
+    out[c2] = a0;
+    out[c2 + 1] = a1;
   } else {
-    for (int P = 0; P < naux; ++P) {
+    for (int P = Pa; P < Pb; ++P) {
       const double wp = __ldg(w + P);
       a0 = fma(wp, B[(int64_t)P * npair + c2], a0);
       if (c2 + 1 < npair) a1 = fma(wp, B[(int64_t)P * npair + c2 + 1], a1);
     }
-    Jp[c2] = a0;
-    if (c2 + 1 < npair) Jp[c2 + 1] = a1;
+    out[c2] = a0;
+    if (c2 + 1 < npair) out[c2 + 1] = a1;
   }
+}
+
+// J[r][c] = sum_y Jp[y][pair(r, c)] (full symmetric N x N, chunks in order).
+__global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n, double *J) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  const int64_t r = i / n, c = i % n;
+  const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
+  const int64_t q = hi * (hi + 1) / 2 + lo;
+  double s = Jp[q];
+  for (int y = 1; y < nsplit; ++y) s += Jp[(int64_t)y * npair + q];
+  J[i] = s;
+}
+
+// aux chunks of the J pass: enough blocks for four per SM, at least 64 P each
+int jpass_split(int64_t npair, int naux) {
+  const int64_t blocks = (npair / 2 + 256) / 256;
+  int sp = (int)std::min<int64_t>(16, (4 * 152 + blocks - 1) / blocks);
+  sp = std::max(1, std::min(sp, naux / 64));
+  return sp;
 }
 
 // Packed lower triangle -> full symmetric N x N.
@@ -71,6 +111,21 @@ __global__ void k_unpack_sym(const double *Jp, int n, double *J) {
   const int64_t r = i / n, c = i % n;
   const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
   J[i] = Jp[hi * (hi + 1) / 2 + lo];
+}
+
+int jpass_fp64(Df *df, double *J, cudaStream_t s) {
+  const int n = df->basis->nbf, naux = df->basis->naux;
+  const int64_t npair = df->npair;
+  if (!df->B64.p) return BQC_E_INVALID;
+  const int sp = jpass_split(npair, naux);
+  if (df->Jp.n < (size_t)sp * npair * 8) return BQC_E_INVALID;
+  k_jpass64<<<dim3((unsigned)((npair / 2 + 256) / 256), (unsigned)sp), 256, 0, s>>>(
+      df->B64.as<double>(), df->w.as<double>(), naux, npair, df->Jp.as<double>());
+  BQC_LAUNCH_CHECK();
+  k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(), sp,
+                                                                         npair, n, J);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
 }
 
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {
@@ -99,12 +154,7 @@ int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s
   BQC_LAUNCH_CHECK();
   df->mark(2, s);
   // J pass
-  k_jpass64<<<(unsigned)((npair / 2 + 256) / 256), 256, 0, s>>>(
-      df->B64.as<double>(), df->w.as<double>(), naux, npair, df->Jp.as<double>());
-  BQC_LAUNCH_CHECK();
-  k_unpack_sym<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(), n,
-                                                                         J);
-  BQC_LAUNCH_CHECK();
+  BQC_TRY(jpass_fp64(df, J, s));
   df->mark(3, s);
   // K = sum_{P,i} X_P,mu i X_P,nu i
   Gemm64Args k;
@@ -131,7 +181,7 @@ size_t df_stored_bytes(int n, int naux, int nocc, bool fp32) {
   const size_t npair = (size_t)n * (n + 1) / 2;
   size_t b = (size_t)naux * naux * 8 + (size_t)naux * npair * 8;  // L, B64
   b += (size_t)naux * n * nocc * 8;                                // X64
-  b += npair * 8 + (size_t)naux * 8 * 2;
+  b += (size_t)jpass_split((int64_t)npair, naux) * npair * 8 + (size_t)naux * 8 * 2;
   if (fp32) {
     b += (size_t)naux * n * mixed_ld(n) * 4;  // B32 (hi part)
     b += (size_t)naux * n * nocc * 4;       // X32
@@ -211,7 +261,8 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
                               s)) != BQC_OK)
       return fail(st);
     if ((st = df->X64.alloc(ctx, (size_t)naux * n * no * 8)) != BQC_OK) return fail(st);
-    if ((st = df->Jp.alloc(ctx, (size_t)npair * 8)) != BQC_OK) return fail(st);
+    if ((st = df->Jp.alloc(ctx, (size_t)jpass_split(npair, naux) * npair * 8)) != BQC_OK)
+      return fail(st);
     if (o.keep_fp32) {
       if ((st = df->B32.alloc(ctx, (size_t)naux * n * mixed_ld(n) * 4)) != BQC_OK)
         return fail(st);
@@ -275,8 +326,9 @@ int bqc_df_phase_ms(bqc_df *df, float *ms, int n) {
   BQC_CUDA_TRY(cudaEventElapsedTime(&t[0], df->ev[1], df->ev[2]));
   BQC_CUDA_TRY(cudaEventElapsedTime(&t[3], df->ev[0], df->ev[1]));
   if (df->mode == BQC_DF_STORED && df->side && df->last_mixed) {
-    // mixed stored build: J pass (side stream, ev2 -> ev5) overlaps the SYRK (ev2 -> ev3)
-    BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[5]));
+    // mixed stored build: J (side stream, ev[j_from] -> ev5) overlaps the
+    // tensor-core passes; K is the SYRK (ev2 -> ev3)
+    BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[df->j_from], df->ev[5]));
     BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[2], df->ev[3]));
   } else {
     BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[2], df->ev[3]));

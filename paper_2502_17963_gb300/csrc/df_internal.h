@@ -48,11 +48,12 @@ struct Df {
   std::unique_ptr<DirectMixed, DirectMixedDeleter> dmixed;  // tensor-core state
   // phase timing (bqc_df_timing)
   bool timing = false, timed = false, last_mixed = false;
+  int j_from = 2;  // event that opens the J phase of the last mixed stored build
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void mark(int i, cudaStream_t s) {
     if (timing && ev[i]) cudaEventRecord(ev[i], s);
   }
-  // side stream of the mixed build: the J pass runs there concurrently with the SYRK
+  // side stream of the mixed build: J runs there concurrently with the tensor-core passes
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   ~Df() {
@@ -74,6 +75,8 @@ int mixed_ld(int n);  // row length of the TF32 shadow (N rounded up to 4)
 int mixed_setup(Df *df, cudaStream_t s);
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
+// J = sum_P w_P B_P from the packed FP64 B and df->w (FP64), full symmetric.
+int jpass_fp64(Df *df, double *J, cudaStream_t s);
 int direct_setup(Df *df, cudaStream_t s);
 size_t direct_mixed_bytes(int n, int naux, int nocc, int bs);
 int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s);

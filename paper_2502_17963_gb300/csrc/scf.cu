@@ -303,12 +303,26 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     BQC_CUDA_TRY(cudaMemcpyAsync(&hv, err + (imax - 1), 8, cudaMemcpyDeviceToHost, s));
     BQC_CUDA_TRY(cudaStreamSynchronize(s));
     emax = std::fabs(hv);
+    if (res->history && res->history_len < res->history_cap) {
+      double *h = res->history + 3 * (size_t)res->history_len++;
+      h[0] = stage;
+      h[1] = emax;
+      h[2] = E;
+    }
     if (stage == BQC_PREC_FP64 && emax < o.diis_tol && have_prev &&
         std::fabs(E - Eprev) < o.energy_tol) {
       converged = true;
       break;
     }
     if (stage != BQC_PREC_FP64) {
+      // Switch to FP64 at stage_tol, or once the mixed stage has reached its
+      // floor: the DIIS error of a mixed Fock matrix cannot fall below about
+      // max|dF| / sqrt(s_min) (s_min the smallest kept overlap eigenvalue;
+      // the orthogonalisation amplifies dF by that much), which in diffuse
+      // bases lies well above stage_tol.  The floor shows as a best error that
+      // stops halving.  Early iterations from the core guess oscillate at
+      // large errors, so stagnation counts only below 1e-2, with a hard
+      // bound of 8 iterations without progress and max_iter / 2 in total.
       ++mixed_iters;
       if (emax < best * 0.5) {
         best = emax;
@@ -316,7 +330,9 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
       } else {
         ++since_best;
       }
-      if (emax < o.stage_tol || since_best >= 4) {
+      const bool at_floor = (since_best >= 3 && best < 1e-2) || since_best >= 8 ||
+                            mixed_iters >= std::max(2, o.max_iter / 2);
+      if (emax < o.stage_tol || at_floor) {
         // switch to FP64: discard the mixed history, redo this iteration in FP64
         stage = BQC_PREC_FP64;
         slot.clear();
@@ -419,11 +435,14 @@ int bqc_scf_run(bqc_ctx *ctx, bqc_df *df, const bqc_scf_opts *opts, bqc_stream_t
     if (o.diis_space <= 0) o.diis_space = 8;
     if (o.orth_thresh <= 0) o.orth_thresh = 1e-8;
   }
-  double *C = out->C_dev, *eps = out->eps_dev, *F = out->F_dev;
+  double *C = out->C_dev, *eps = out->eps_dev, *F = out->F_dev, *hist = out->history;
+  const int cap = out->history_cap;
   *out = bqc_scf_result{};
   out->C_dev = C;
   out->eps_dev = eps;
   out->F_dev = F;
+  out->history = hist;
+  out->history_cap = hist ? std::max(cap, 0) : 0;
   return scf_run(ctx, df, o, (cudaStream_t)stream, out);
 }
 

@@ -2,9 +2,10 @@
 //
 // Requests of different molecule sizes arrive at any time.  A request is
 // admitted as soon as a slot is free and the HBM ledger has room for its
-// predicted footprint; every admitted request runs its basis setup, DF build
-// and SCF on its own CUDA stream, so the work of several molecules overlaps
-// on the device while new requests keep arriving.  All device memory comes
+// predicted footprint (queue order, with bounded backfill past a head that
+// does not fit); every admitted request runs its basis setup, DF build and
+// SCF on its own CUDA stream, prioritised by molecule size, so the work of
+// several molecules overlaps on the device while new requests keep arriving.  All device memory comes
 // from one arena reserved when the server is created, so the serving loop
 // never calls cudaMalloc / cudaFree (both can synchronise the device and
 // would serialise the slots).
@@ -108,6 +109,7 @@ struct Request {
   std::vector<double> exps[2], coefs[2];
   int nbf = 0, naux = 0, nocc = 0;
   size_t footprint = 0;
+  int skipped = 0;  // times a later request was admitted ahead of this one
   bool done = false;
   bqc_serve_result res{};
 };
@@ -130,6 +132,7 @@ struct bqc_server {
   uint64_t next_id = 1;
   int pending = 0;
   bool stop = false;
+  int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range
   std::chrono::steady_clock::time_point t0;
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -188,30 +191,68 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
   r->res.energy = res.energy;
   r->res.diis_err = res.diis_err;
   r->res.iterations = res.iterations;
+  r->res.iterations_mixed = res.iterations_mixed;
+}
+
+// Stream priority of a request: one level above the lowest per halving of N
+// below 1536, so a small molecule's blocks are scheduled ahead of a large
+// one's when both are pending (running blocks are never preempted).
+static int request_priority(const bqc_server *srv, int nbf) {
+  if (srv->opts.policy == BQC_SERVE_FIFO) return srv->prio_least;
+  int lvl = 0;
+  for (int m = 1536; lvl < srv->prio_least - srv->prio_greatest && 2 * nbf <= m; m /= 2) ++lvl;
+  return srv->prio_least - lvl;
+}
+
+// Next request to admit (called with srv->mu held), or nullptr.  The queue
+// head is admitted when it fits the ledger.  Otherwise, with backfill, the
+// first later request that fits is admitted instead and the head's skip
+// count grows; once it reaches max_skips nothing passes the head any more.
+static Request *pick_request(bqc_server *srv) {
+  if (srv->queue.empty()) return nullptr;
+  auto fits = [&](const Request *r) { return srv->ledger + r->footprint <= srv->budget; };
+  Request *h = srv->reqs[srv->queue.front()].get();
+  if (fits(h)) {
+    srv->queue.pop_front();
+    return h;
+  }
+  const int max_skips = srv->opts.max_skips > 0 ? srv->opts.max_skips : 8;
+  if (srv->opts.policy == BQC_SERVE_FIFO || h->skipped >= max_skips) return nullptr;
+  for (auto it = srv->queue.begin() + 1; it != srv->queue.end(); ++it) {
+    Request *r = srv->reqs[*it].get();
+    if (fits(r)) {
+      srv->queue.erase(it);
+      ++h->skipped;
+      return r;
+    }
+  }
+  return nullptr;
 }
 
 static void worker_main(bqc_server *srv) {
   cudaSetDevice(srv->ctx->device);
-  cudaStream_t s;
-  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  // one stream per priority level, created on first use
+  std::vector<cudaStream_t> streams(srv->prio_least - srv->prio_greatest + 1, nullptr);
   while (true) {
     Request *r = nullptr;
     {
       std::unique_lock<std::mutex> lk(srv->mu);
-      srv->cv_work.wait(lk, [&] {
-        if (srv->stop) return true;
-        if (srv->queue.empty()) return false;
-        Request *h = srv->reqs[srv->queue.front()].get();
-        return srv->ledger + h->footprint <= srv->budget;  // FIFO admission by HBM ledger
-      });
-      if (srv->stop && srv->queue.empty()) break;
-      if (srv->stop) break;
-      r = srv->reqs[srv->queue.front()].get();
-      srv->queue.pop_front();
+      while (!srv->stop && !(r = pick_request(srv))) srv->cv_work.wait(lk);
+      if (!r) break;
       srv->ledger += r->footprint;
       r->res.t_admit = srv->now();
+      r->res.priority = request_priority(srv, r->nbf);
     }
-    run_request(srv, r, s);
+    cudaStream_t &s = streams[srv->prio_least - r->res.priority];
+    if (!s && cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, r->res.priority) != cudaSuccess) {
+      cudaGetLastError();
+      s = nullptr;
+    }
+    if (s) {
+      run_request(srv, r, s);
+    } else {
+      r->res.status = BQC_E_CUDA;
+    }
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       srv->ledger -= r->footprint;
@@ -222,7 +263,8 @@ static void worker_main(bqc_server *srv) {
     srv->cv_work.notify_all();
     srv->cv_done.notify_all();
   }
-  cudaStreamDestroy(s);
+  for (cudaStream_t s : streams)
+    if (s) cudaStreamDestroy(s);
 }
 
 }  // namespace bqc
@@ -252,9 +294,14 @@ int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out)
   o.scf.max_iter = 100;
   o.scf.diis_space = 8;
   o.scf.orth_thresh = 1e-8;
+  o.policy = BQC_SERVE_BACKFILL;
+  o.max_skips = 8;
   if (opts) o = *opts;
   if (o.max_slots <= 0) o.max_slots = 4;
+  if (o.policy != BQC_SERVE_FIFO) o.policy = BQC_SERVE_BACKFILL;
+  if (o.max_skips <= 0) o.max_skips = 8;
   srv->opts = o;
+  BQC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&srv->prio_least, &srv->prio_greatest));
   size_t budget = o.hbm_budget ? o.hbm_budget : ctx->budget;
   if (!budget) {
     size_t fr = 0, tot = 0;

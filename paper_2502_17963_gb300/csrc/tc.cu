@@ -98,11 +98,17 @@ __device__ __forceinline__ float tf32r(float x) {
 //    group of kGroupKb k-blocks; TMEM holds two accumulators, and while the
 //    MMA warp fills one, eight epilogue warps drain the other into register
 //    accumulators with round-to-nearest adds (X pass: FP32; SYRK:
-//    float-float, the compensation term kept in spare TMEM columns).
+//    float-float, the compensation term kept in spare TMEM columns).  Within
+//    a chain the cross terms go first, while the accumulator is still small,
+//    so that only the hi*hi MMAs add into a full-size accumulator.  At the
+//    end of the chain the bias is what decides the SCF's error floor in
+//    mixed precision (the orthogonalisation amplifies a relative shift of K
+//    by the inverse square root of the smallest overlap eigenvalue).
 
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, 8 epilogue warps
-constexpr int kGroupKb = 4;                    // k-blocks (of 32) per TMEM chain
+constexpr int kGroupKb = 2;   // k-blocks (of 32) per TMEM chain: X pass, TRMM
+constexpr int kGroupKbS = 2;  // SYRK (its float-float drain costs more per chain)
 
 struct XpassParams {
   int64_t rows;      // Naux * N  (M of the GEMM)
@@ -208,13 +214,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t ah = sbase + s * stage_bytes, al = ah + a_bytes;
             const uint32_t ch = ah + NS * a_bytes, cl = ch + c_bytes;
+            if (SPLIT == 3) {
+              // cross terms first: their running sum stays ~2^-11 of the
+              // result, so the accumulator's truncation there is negligible;
+              // then the hi*hi terms
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const uint32_t first = ((kb - kb0) | k4) != 0;
-              mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, first);
-              if (SPLIT == 3) {
-                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(cl + k4 * 32), idesc, 1);
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint32_t acc = ((kb - kb0) | k4) != 0;
+                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(cl + k4 * 32), idesc, acc);
                 mma_tf32(d, sdesc_sw128(al + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, 1);
+              }
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4)
+                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, 1);
+            } else {
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint32_t acc = ((kb - kb0) | k4) != 0;
+                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, acc);
               }
             }
             mma_commit(empty0 + 8 * s);
@@ -436,13 +453,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         int nkb;
         int64_t P0;
         chunk_kb(it / p.ntri, P0, nkb);
-        for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKb, ++g) {
+        for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKbS, ++g) {
           const int b = (int)(g & 1);
           if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 24);
           if (!ok) break;
           tc_fence_after();
           const uint32_t d = tbase + b * kBM;
-          const int kb1 = min(nkb, kb0 + kGroupKb);
+          const int kb1 = min(nkb, kb0 + kGroupKbS);
           for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
             const int s = (int)(kg % p.stages);
             ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / p.stages) & 1), p.flag, 22);
@@ -450,13 +467,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t hm = sbase + s * stage_bytes, hn = hm + kAStage;
             const uint32_t lm = hm + 2 * kAStage, ln = hm + 3 * kAStage;
+            if (SPLIT == 3) {  // cross terms first, as in the X pass
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const uint32_t first = ((kb - kb0) | k4) != 0;
-              mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, first);
-              if (SPLIT == 3) {
-                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(ln + k4 * 32), idesc, 1);
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint32_t acc = ((kb - kb0) | k4) != 0;
+                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(ln + k4 * 32), idesc, acc);
                 mma_tf32(d, sdesc_sw128(lm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, 1);
+              }
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4)
+                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, 1);
+            } else {
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint32_t acc = ((kb - kb0) | k4) != 0;
+                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, acc);
               }
             }
             mma_commit(empty0 + 8 * s);
@@ -483,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int c = 0; c < kSyCols; c += 16) tmem_st16(tbase + lane_base + kLoCol + h * kSyCols + c, z);
       }
-      for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKb, ++g) {
+      for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKbS, ++g) {
         const int b = (int)(g & 1);
         if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 23);
         __syncwarp();
@@ -664,13 +689,21 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc_fence_after();
               const uint32_t xh = sbase + st * stage_bytes, lh = xh + kAStage;
               const uint32_t xl = xh + 2 * kAStage, ll = xh + 3 * kAStage;
+              if (SPLIT == 3) {  // cross terms first, as in the X pass
 #pragma unroll
-              for (int k4 = 0; k4 < 4; ++k4) {
-                const uint32_t first = ((kb - kb0) | k4) != 0;
-                mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, first);
-                if (SPLIT == 3) {
-                  mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(ll + k4 * 32), idesc, 1);
+                for (int k4 = 0; k4 < 4; ++k4) {
+                  const uint32_t acc = ((kb - kb0) | k4) != 0;
+                  mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(ll + k4 * 32), idesc, acc);
                   mma_tf32(d, sdesc_sw128(xl + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, 1);
+                }
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4)
+                  mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, 1);
+              } else {
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                  const uint32_t acc = ((kb - kb0) | k4) != 0;
+                  mma_tf32(d, sdesc_sw128(xh + k4 * 32), sdesc_sw128(lh + k4 * 32), idesc, acc);
                 }
               }
               mma_commit(empty0 + 8 * st);
@@ -872,9 +905,25 @@ static MixedPlan mixed_plan(int n, int naux, int nocc, int nsm) {
   }
   m.ntile = (n + kBM - 1) / kBM;
   m.ntri = m.ntile * (m.ntile + 1) / 2;
-  // work items about two per SM, chunks of at least 16 aux functions
+  // work items (tile, aux chunk): at least two per SM, chunks of at least 16
+  // aux functions, and the chunk count whose items split most evenly over
+  // the persistent CTAs (the makespan is ceil(items / nsm) items)
   int nchunk = std::max(1, (nsm + m.ntri - 1) / m.ntri);
   while (nchunk * m.ntri < 2 * nsm && nchunk * 16 < naux) ++nchunk;
+  {
+    int best = nchunk;
+    double best_eff = 0.0;
+    const int cmax = std::max(2 * nchunk, nchunk + 8);
+    for (int c = nchunk; c <= cmax && c * 16 <= std::max(16, naux); ++c) {
+      const double items = (double)c * m.ntri;
+      const double eff = items / ((double)((c * m.ntri + nsm - 1) / nsm) * nsm);
+      if (eff > best_eff + 1e-3) {
+        best_eff = eff;
+        best = c;
+      }
+    }
+    nchunk = best;
+  }
   nchunk = std::min(nchunk, std::max(1, naux));
   m.ppc = (naux + nchunk - 1) / nchunk;
   m.nchunk = (naux + m.ppc - 1) / m.ppc;
@@ -956,7 +1005,13 @@ int mixed_setup(Df *df, cudaStream_t s) {
   const MixedPlan &m = ms->plan;
   if (m.xp_stages[1] < 2 || m.sy_stages[1] < 2) return BQC_E_UNSUPPORTED;
   if (!df->side) {
-    BQC_CUDA_TRY(cudaStreamCreateWithFlags(&df->side, cudaStreamNonBlocking));
+    // the side stream inherits the caller's priority (serving ranks requests by it)
+    int prio = 0;
+    if (s && cudaStreamGetPriority(s, &prio) != cudaSuccess) {
+      cudaGetLastError();
+      prio = 0;
+    }
+    BQC_CUDA_TRY(cudaStreamCreateWithPriority(&df->side, cudaStreamNonBlocking, prio));
     BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork, cudaEventDisableTiming));
     BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
   }
@@ -1086,6 +1141,14 @@ int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, 
   return BQC_OK;
 }
 
+// w comes fused from the X pass in both mixed precisions (FP32 row partials
+// of X C, summed in FP64).  The J pass then runs on the side stream,
+// concurrently with the SYRK: 3xTF32 reads the packed FP64 B (FP64 FMAs),
+// single-pass TF32 reads the TF32 shadow.  Reading B in FP64 matters: with
+// the TF32 split of B in the J pass, max|dJ| is only ~1e-6, but in a diffuse
+// basis the orthogonalisation amplifies it (by up to 1/sqrt(s_min)) into a
+// DIIS error of ~1e-4, which would set the mixed SCF's error floor; the
+// error of the fused w, a smooth Coulomb-like perturbation, stays ~1e-7.
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   if (!ms) return BQC_E_INVALID;
@@ -1094,27 +1157,30 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux;
   const int64_t rows = (int64_t)naux * n;
+  const bool j64 = split == 3 && df->B64.p;
   BQC_TRY(mixed_xpass(df, C, split, s, &ms->mapAh, &ms->mapAl, rows, df->X32.as<float>(),
                       ms->Xl.as<float>(), df->w.as<double>()));
   df->mark(2, s);
-  // J pass (HBM-bound) on the side stream, concurrent with the SYRK
+  df->j_from = 2;
   cudaStream_t js = s;
   if (df->side) {
     BQC_CUDA_TRY(cudaEventRecord(df->fork, s));
     BQC_CUDA_TRY(cudaStreamWaitEvent(df->side, df->fork, 0));
     js = df->side;
   }
-  const dim3 jgrid((unsigned)((n + 1) / 2), (unsigned)(((n - 1) / 4 + 2 + kJThreads - 1) / kJThreads));
-  if (split == 3)
-    k_jpass_tf32<3><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), ms->Bl.as<float>(),
+  if (j64) {
+    BQC_TRY(jpass_fp64(df, J, js));
+  } else {
+    const dim3 jgrid((unsigned)((n + 1) / 2),
+                     (unsigned)(((n - 1) / 4 + 2 + kJThreads - 1) / kJThreads));
+    k_jpass_tf32<1><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), nullptr,
                                                  ms->w32.as<float>(), naux, n, m.ld,
                                                  df->Jp.as<double>());
-  else
-    k_jpass_tf32<1><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), nullptr, ms->w32.as<float>(),
-                                                 naux, n, m.ld, df->Jp.as<double>());
-  BQC_LAUNCH_CHECK();
-  k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, js>>>(df->Jp.as<double>(), n, J);
-  BQC_LAUNCH_CHECK();
+    BQC_LAUNCH_CHECK();
+    k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, js>>>(df->Jp.as<double>(),
+                                                                             n, J);
+    BQC_LAUNCH_CHECK();
+  }
   if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
   BQC_TRY(mixed_syrk(df, split, &ms->mapXh, &ms->mapXl, naux, K, s));
   df->mark(3, s);

@@ -3,8 +3,10 @@
 Per molecule and precision two checks:
   * kernel exactness: against an FP64 evaluation of the same split operands
     (TF32X3: X = Bh Ch + Bh Cl + Bl Ch with hi/lo TF32 parts; TF32: X = Bh Ch).
-    The remaining differences are the FP32 accumulation of X (relative to
-    XA = |B| |C|, which exceeds |X| by the cancellation in B C) and, for
+    The J pass reads the FP64 B for TF32X3 (w from the split X either way).
+    The remaining differences are the FP32
+    accumulation of X (relative to XA = |B| |C|, which exceeds |X| by the
+    cancellation in B C) and, for
     TF32, the rounding of X before the SYRK.  They are bounded elementwise by
     a constant times the absolute-value contractions
     KA = sum_{P,i} (|X| XA^T + XA |X|^T) for K and JA = sum_P |w|_P |B_P| for
@@ -74,9 +76,10 @@ def test_jk_mixed(gpu_ctx, bqc, name, prec):
         X = np.einsum("pmn,ni->pmi", Bh, Ch, optimize=True)
         Bs = Bh
     Cf = C.astype(np.float32).astype(np.float64)
-    w = np.einsum("pmi,mi->p", X, Cf, optimize=True)
     Ke = np.einsum("pmi,pni->mn", X, X, optimize=True)
-    Je = np.einsum("p,pmn->mn", w, Bs, optimize=True)
+    w = np.einsum("pmi,mi->p", X, Cf, optimize=True)
+    # TF32X3's J pass reads the FP64 B, single-pass TF32's the TF32 shadow
+    Je = np.einsum("p,pmn->mn", w, B if prec == 2 else Bs, optimize=True)
     Xa = np.abs(X)
     XA = np.einsum("pmn,ni->pmi", np.abs(B), np.abs(C), optimize=True)
     KA = np.einsum("pmi,pni->mn", Xa, XA, optimize=True)

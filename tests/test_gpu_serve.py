@@ -74,3 +74,63 @@ def test_not_converged_status(gpu_ctx, bqc):
     r = srv.poll(t)
     assert r["status"] == -4 and r["iterations"] == 2
     srv.close()
+
+
+def _sampled_requests(count=20, nmax=6):
+    """The first `count` requests of the seed-2025 Poisson stream with n <= nmax
+    (geometry seed = request id), as (name, Molecule)."""
+    out = []
+    for _, n, rid in workload.serving_stream(nreq=2000):
+        if n <= nmax:
+            out.append((f"r{rid}", workload.water_cluster(n, seed=rid)))
+        if len(out) == count:
+            break
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-8)])
+def test_alone_equals_mix_sampled_stream(gpu_ctx, bqc, prec, tol):
+    reqs = _sampled_requests()
+    assert len(reqs) == 20 and len({len(m.Z) for _, m in reqs}) > 2
+    srv = bqc.Server(gpu_ctx, max_slots=1, prec=prec, hbm_budget=8 << 30)
+    alone = {}
+    for name, mol in reqs:
+        t = srv.submit(mol)
+        srv.drain(600)
+        alone[name] = srv.poll(t)
+    srv.close()
+    srv = bqc.Server(gpu_ctx, max_slots=6, prec=prec, hbm_budget=8 << 30)
+    ts = {name: srv.submit(mol) for name, mol in reqs}
+    srv.drain(900)
+    mix = {name: srv.poll(t) for name, t in ts.items()}
+    srv.close()
+    for name, _ in reqs:
+        a, m = alone[name], mix[name]
+        assert a["status"] == 0 and m["status"] == 0, (name, a, m)
+        assert abs(a["energy"] - m["energy"]) <= tol, (name, a["energy"], m["energy"])
+        assert a["iterations"] == m["iterations"]
+    spans = sorted((r["t_admit"], r["t_done"]) for r in mix.values())
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_backfill_admission_and_priority(gpu_ctx, bqc, policy):
+    big, small = workload.water_cluster(6), workload.single_water()
+    fb = bqc.serve_footprint(150, 450, 30)
+    fs = bqc.serve_footprint(26, 92, 5)
+    assert fs < fb
+    # two large requests never fit together, a large and a small one do
+    srv = bqc.Server(gpu_ctx, max_slots=3, prec=2, hbm_budget=2 * fb - 1, policy=policy)
+    t1, t2, t3 = srv.submit(big), srv.submit(big), srv.submit(small)
+    srv.drain(600)
+    r1, r2, r3 = srv.poll(t1), srv.poll(t2), srv.poll(t3)
+    srv.close()
+    assert r1["status"] == 0 and r2["status"] == 0 and r3["status"] == 0
+    assert r1["energy"] == r2["energy"]
+    if policy == bqc.SERVE_BACKFILL:
+        # the small request was admitted past the waiting large one, at a higher priority
+        assert r3["t_admit"] < r2["t_admit"]
+        assert r3["priority"] <= r1["priority"]
+    else:
+        assert r3["t_admit"] >= r2["t_admit"]
+        assert r3["priority"] == r1["priority"] == r2["priority"]
