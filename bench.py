@@ -297,7 +297,10 @@ def run_direct(args):
                                             "Schwarz 1e-10"},
             "phases_ms": {"pass1_integrals_gamma_X": pm[0], "metric_solve_and_K": pm[1],
                           "pass2_integrals_J": pm[2], "prep": pm[3]},
-            "setup_s": setup, "device_bytes": df.device_bytes, "clocks": clk}
+            "setup_s": setup, "device_bytes": df.device_bytes, "clocks": clk,
+            "screening": dict(zip(("triplets_considered", "triplets_kept"), df.screening()))}
+    sc = line["screening"]
+    sc["survival"] = sc["triplets_kept"] / max(1, sc["triplets_considered"])
     print(json.dumps(line), flush=True)
 
 

@@ -158,6 +158,9 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
 int bqc_df_destroy(bqc_df *df);
 /* Mode actually built and bytes of device memory held. */
 int bqc_df_info(const bqc_df *df, int *mode, size_t *device_bytes);
+/* Schwarz screening of the 3-centre integrals (Sec. 2.2): shell triplets
+ * (aux shell, orbital shell pair) considered and kept (Q_P Q_mu nu >= tau). */
+int bqc_df_screening(const bqc_df *df, int64_t *candidates, int64_t *survivors);
 /* Copy B (Naux x Npair packed, FP64, stored mode) into a device buffer; or
  * the Cholesky factor L (Naux x Naux, lower, zeros above) when which = 1.  Async. */
 int bqc_df_copy(const bqc_df *df, int which, double *out_dev, bqc_stream_t stream);

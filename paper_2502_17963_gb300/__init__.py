@@ -112,6 +112,7 @@ _SIGS = {
     "bqc_df_build": (ip, [vp, vp, ctypes.POINTER(bqc_df_opts), vp, ctypes.POINTER(vp)]),
     "bqc_df_destroy": (ip, [vp]),
     "bqc_df_info": (ip, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
+    "bqc_df_screening": (ip, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "bqc_df_copy": (ip, [vp, ip, vp, vp]),
     "bqc_jk": (ip, [vp, vp, ip, ip, vp, vp, vp]),
     "bqc_jk_host": (ip, [vp, vp, ip, ip, vp, vp, vp]),
@@ -320,6 +321,12 @@ class DF:
         m, b = ctypes.c_int(), ctypes.c_size_t()
         check(lib().bqc_df_info(h, ctypes.byref(m), ctypes.byref(b)), "bqc_df_info")
         self.mode, self.device_bytes = m.value, b.value
+
+    def screening(self):
+        """(shell triplets considered, kept) by the Schwarz screening."""
+        c, k = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().bqc_df_screening(self.h, ctypes.byref(c), ctypes.byref(k)), "bqc_df_screening")
+        return c.value, k.value
 
     def copy(self, which: int = 0, stream=None):
         """B (Naux, Npair) for which=0, the Cholesky factor L (Naux, Naux) for which=1."""

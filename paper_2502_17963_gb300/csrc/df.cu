@@ -291,6 +291,13 @@ int bqc_df_info(const bqc_df *df, int *mode, size_t *bytes) {
   return BQC_OK;
 }
 
+int bqc_df_screening(const bqc_df *df, int64_t *candidates, int64_t *survivors) {
+  if (!df) return BQC_E_INVALID;
+  if (candidates) *candidates = df->plan.candidates;
+  if (survivors) *survivors = df->plan.survivors;
+  return BQC_OK;
+}
+
 int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
   if (!df || !out) return BQC_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;

@@ -107,7 +107,7 @@ __device__ __forceinline__ float tf32r(float x) {
 
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, 8 epilogue warps
-constexpr int kGroupKb = 2;   // k-blocks (of 32) per TMEM chain: X pass, TRMM
+constexpr int kGroupKb = 4;   // k-blocks (of 32) per TMEM chain: X pass, TRMM
 constexpr int kGroupKbS = 2;  // SYRK (its float-float drain costs more per chain)
 
 struct XpassParams {
