@@ -54,9 +54,13 @@ int make_tmap_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *
     set_error("cuTensorMapEncodeTiled unavailable", __FILE__, __LINE__);
     return BQC_E_CUDA;
   }
-  cuuint32_t estr[3] = {1, 1, 1};
-  cuuint64_t d[3], s[2];
-  cuuint32_t b[3];
+  if (rank < 1 || rank > 5) {
+    set_error("tensor map rank out of range", __FILE__, __LINE__);
+    return BQC_E_INVALID;
+  }
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  cuuint64_t d[5], s[4];
+  cuuint32_t b[5];
   for (int i = 0; i < rank; ++i) {
     d[i] = dims[i];
     b[i] = box[i];
@@ -107,8 +111,8 @@ __device__ __forceinline__ float tf32r(float x) {
 
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, 8 epilogue warps
-constexpr int kGroupKb = 4;   // k-blocks (of 32) per TMEM chain: X pass, TRMM
-constexpr int kGroupKbS = 2;  // SYRK (its float-float drain costs more per chain)
+constexpr int kGroupKb = 4;   // k-blocks (of 32) per TMEM chain: X pass (contraction N)
+constexpr int kGroupKbS = 2;  // SYRK and TRMM (contractions of Naux x nocc and Naux)
 
 struct XpassParams {
   int64_t rows;      // Naux * N  (M of the GEMM)
@@ -123,10 +127,10 @@ struct XpassParams {
   float *wpart;      // [2 * ncg][rows] partial w per row
   int *flag;
   // transposed epilogue (EPI = 1, direct mode): rows are (mu, q) with q the
-  // aux function within a block of bk, written to X^T[mu][i][q0 + q] with
-  // row length naux_ld
+  // aux function within a block of bk, written to X^T(mu, i, P = q0 + q)
+  // stored as [P block][i][mu][32] (xrows = ldx * N rows per P block)
   int bk, q0, bkv;   // bkv: valid rows per mu (a ragged last sub-block)
-  int64_t naux_ld;
+  int64_t xrows;
 };
 
 // Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
@@ -302,12 +306,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // consecutive lanes hold consecutive q of one mu: coalesced per column
         const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
         const int col = cg * XN + h * HALF;
-        const int64_t base = (mu * p.ldx + col) * p.naux_ld + qq;
+        const int64_t base = ((qq >> 5) * p.xrows + (int64_t)col * p.n + mu) * 32 + (qq & 31);
+        const int64_t step = (int64_t)p.n * 32;
 #pragma unroll
         for (int c = 0; c < HALF; ++c) {
           const float hv = tf32r(acc[c]);
-          p.Xh[base + (int64_t)c * p.naux_ld] = hv;
-          if (SPLIT == 3) p.Xl[base + (int64_t)c * p.naux_ld] = tf32r(acc[c] - hv);
+          p.Xh[base + (int64_t)c * step] = hv;
+          if (SPLIT == 3) p.Xl[base + (int64_t)c * step] = tf32r(acc[c] - hv);
         }
       }
     }
@@ -347,9 +352,11 @@ struct SyrkParams {
   int stages;
   double *part;  // [chunk][ntri][128][128]
   int *flag;
-  // 2-D operand mode (direct mode): X^T as rows mu x K with K = (i, P)
-  // contiguous; chunks are ranges of kb_per_chunk k-blocks of kb_total
+  // blocked operand mode (direct mode): Y^T stored as [P block][i][mu][32];
+  // rows mu, K = (i, P) with k-block kb = i * npb + P block; chunks are ranges
+  // of kb_per_chunk k-blocks of kb_total
   int mode2d;
+  int npb;
   int64_t kb_total;
   int64_t kb_per_chunk;
 };
@@ -426,12 +433,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a = sbase + s * stage_bytes, bar = full0 + 8 * s;
           mbar_arrive_expect_tx(bar, stage_bytes);
           if (p.mode2d) {
-            const int k0 = (int)((P0 + kb) * 32);
-            tma_load_2d(a, &mapXh, bar, k0, tm * kBM);
-            tma_load_2d(a + kAStage, &mapXh, bar, k0, tn * kBM);
+            // one box = 128 consecutive mu of one (i, P block): 16 KB contiguous
+            const int64_t kk = P0 + kb;
+            const int pb = (int)(kk % p.npb), ii = (int)(kk / p.npb);
+            tma_load_4d(a, &mapXh, bar, 0, tm * kBM, ii, pb);
+            tma_load_4d(a + kAStage, &mapXh, bar, 0, tn * kBM, ii, pb);
             if (SPLIT == 3) {
-              tma_load_2d(a + 2 * kAStage, &mapXl, bar, k0, tm * kBM);
-              tma_load_2d(a + 3 * kAStage, &mapXl, bar, k0, tn * kBM);
+              tma_load_4d(a + 2 * kAStage, &mapXl, bar, 0, tm * kBM, ii, pb);
+              tma_load_4d(a + 3 * kAStage, &mapXl, bar, 0, tn * kBM, ii, pb);
             }
           } else {
             const int P = (int)P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
@@ -594,9 +603,8 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nch
 // and writes columns [pt*128, pt*128+128), which later (smaller) tiles never
 // read, so the product can overwrite X.
 struct TrmmParams {
-  int64_t rows;      // N * ldx
+  int64_t rows;      // N * ldx rows r = i * N + mu of X^T, stored as [P block][r][32]
   int naux;          // columns (P and Q)
-  int64_t ld;        // row length of X (= naux)
   int ntp;           // P tiles of 128
   int stages;
   int64_t mtiles;
@@ -657,10 +665,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             const uint32_t a = sbase + st * stage_bytes, bar = full0 + 8 * st;
             mbar_arrive_expect_tx(bar, stage_bytes);
-            tma_load_2d(a, &mapXh, bar, kb * 32, m0);
+            tma_load_3d(a, &mapXh, bar, 0, m0, kb);
             tma_load_2d(a + kAStage, &mapLh, bar, kb * 32, pt * kBM);
             if (SPLIT == 3) {
-              tma_load_2d(a + 2 * kAStage, &mapXl, bar, kb * 32, m0);
+              tma_load_3d(a + 2 * kAStage, &mapXl, bar, 0, m0, kb);
               tma_load_2d(a + 3 * kAStage, &mapLl, bar, kb * 32, pt * kBM);
             }
           }
@@ -674,14 +682,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = blockIdx.x; t < p.mtiles && ok; t += gridDim.x) {
         for (int pt = p.ntp - 1; pt >= 0 && ok; --pt) {
           const int nkb = kblocks_of(pt);
-          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKb, ++g) {
+          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKbS, ++g) {
             const int b = (int)(g & 1);
             if (g >= 2)
               ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 34);
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tbase + b * kBM;
-            const int kb1 = min(nkb, kb0 + kGroupKb);
+            const int kb1 = min(nkb, kb0 + kGroupKbS);
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
               const int st = (int)(kg % p.stages);
               ok = mbar_wait(full0 + 8 * st, (uint32_t)((kg / p.stages) & 1), p.flag, 32);
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float acc[HALF];
 #pragma unroll
         for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
-        for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKb, ++g) {
+        for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKbS, ++g) {
           const int b = (int)(g & 1);
           if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 33);
           __syncwarp();
@@ -742,14 +750,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t row = t * kBM + q * 32 + lane;
         const int col0 = pt * kBM + h * HALF;
         if (ok && row < p.rows) {
-          float *yh = p.Xh + row * p.ld + col0;
-          float *yl = p.Xl + row * p.ld + col0;
+          // columns col0 .. col0 + HALF - 1 span HALF / 32 P blocks of 32
 #pragma unroll
           for (int c = 0; c < HALF; ++c) {
-            if (col0 + c < p.naux) {
+            const int P = col0 + c;
+            if (P < p.naux) {
+              const int64_t e = ((int64_t)(P >> 5) * p.rows + row) * 32 + (P & 31);
               const float hv = tf32r(acc[c]);
-              yh[c] = hv;
-              if (SPLIT == 3) yl[c] = tf32r(acc[c] - hv);
+              p.Xh[e] = hv;
+              if (SPLIT == 3) p.Xl[e] = tf32r(acc[c] - hv);
             }
           }
         }
@@ -1099,7 +1108,7 @@ int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtens
   p.bk = 0;
   p.q0 = 0;
   p.bkv = 0;
-  p.naux_ld = 0;
+  p.xrows = 0;
   BQC_TRY(dispatch_xn(m.xn, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl, grid, s));
   if (w_out) {
     k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
@@ -1127,6 +1136,7 @@ int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, 
   q.part = df->Kpart.as<double>();
   q.flag = df->ctx->flag;
   q.mode2d = 0;
+  q.npb = 0;
   q.kb_total = 0;
   q.kb_per_chunk = 0;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
@@ -1198,25 +1208,62 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
 
 namespace bqc {
 
-// raw (Q|mu nu) of aux rows [qs, qs + nq) of a packed FP64 block -> split
-// shadows laid out [mu][q][ld] (q < bs; rows q >= nq are zero).
-__global__ void k_expand_raw_mu(const double *__restrict__ raw, int64_t npair, int n, int ld,
-                                int bs, int qs, int nq, float *__restrict__ Rh,
-                                float *__restrict__ Rl) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tot = (int64_t)n * bs * ld;
-  if (e >= tot) return;
-  const int64_t mu = e / ((int64_t)bs * ld), rem = e % ((int64_t)bs * ld);
-  const int q = (int)(rem / ld), nu = (int)(rem % ld);
-  float h = 0.0f, l = 0.0f;
-  if (q < nq && nu < n) {
-    const int64_t hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-    const float f = (float)raw[(int64_t)(qs + q) * npair + hi * (hi + 1) / 2 + lo];
-    h = tf32r(f);
-    l = tf32r(f - h);
+// Raw FP64 block (packed lower triangles, rows qs .. qs + nq of the block) ->
+// split TF32 shadows laid out mu-major, Rh/Rl[mu][q][nu], so that the X-pass
+// epilogue can write X^T[mu][i][q] with coalesced stores.  One block
+// (32 x 8 threads) per 32 x 32 tile pair (I >= J) of the symmetric B_q and
+// one aux row q: the packed lower triangle is read once with coalesced rows
+// (tri(mu) + nu is contiguous in nu), and the tile and its mirror image are
+// written through a padded shared-memory transpose, so the writes are
+// coalesced too.  Rows are zero-padded to ld; rows q >= nq are zero.
+__global__ void __launch_bounds__(256) k_expand_raw_mu_t(const double *__restrict__ raw,
+                                                         int64_t npair, int n, int ld, int bs,
+                                                         int qs, int nq, float *__restrict__ Rh,
+                                                         float *__restrict__ Rl) {
+  const int q = blockIdx.y;
+  const int t = blockIdx.x;
+  int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  __shared__ float th[32][33], tl[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double *rq = raw + (int64_t)(qs + q) * npair;
+#pragma unroll
+  for (int r = ty; r < 32; r += 8) {
+    const int mu = I * 32 + r, nu = J * 32 + tx;
+    float h = 0.0f, l = 0.0f;
+    if (q < nq && mu < n && nu < n) {
+      const int64_t hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+      const float f = (float)rq[hi * (hi + 1) / 2 + lo];
+      h = tf32r(f);
+      l = tf32r(f - h);
+    }
+    th[r][tx] = h;
+    tl[r][tx] = l;
   }
-  Rh[e] = h;
-  if (Rl) Rl[e] = l;
+  __syncthreads();
+  const int64_t row = (int64_t)bs * ld;
+#pragma unroll
+  for (int r = ty; r < 32; r += 8) {
+    const int mu = I * 32 + r, nu = J * 32 + tx;
+    if (mu < n && nu < ld) {
+      const int64_t e = (int64_t)mu * row + (int64_t)q * ld + nu;
+      Rh[e] = th[r][tx];
+      if (Rl) Rl[e] = tl[r][tx];
+    }
+  }
+  if (I != J) {
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+      const int mu = J * 32 + r, nu = I * 32 + tx;
+      if (mu < n && nu < ld) {
+        const int64_t e = (int64_t)mu * row + (int64_t)q * ld + nu;
+        Rh[e] = th[tx][r];
+        if (Rl) Rl[e] = tl[tx][r];
+      }
+    }
+  }
 }
 
 // FP64 L^{-1} (n x n) -> split shadows with rows padded to ld (zeros beyond n).
@@ -1242,7 +1289,7 @@ struct DirectMixed {
   int tr_stages[2];
   size_t tr_smem[2];
   int64_t kb_total;    // SYRK k-blocks (ldx * naux_ld / 32)
-  int naux_ld;         // row length of X^T and L^{-1} shadows (Naux rounded to 4: TMA strides)
+  int naux_ld;         // Naux rounded up to 32: P blocks of X^T, row length of the L^{-1} shadows
   int sy_nchunk;
   int64_t sy_kbpc;
   CUtensorMap mapRh, mapRl, mapCh, mapCl, mapXAh, mapXAl, mapLh, mapLl, mapYh, mapYl;
@@ -1278,9 +1325,9 @@ int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s) {
     dm->tr_stages[k] = (int)std::min<size_t>(8, avail / st);
     dm->tr_smem[k] = dm->tr_stages[k] * st + 1024 + 256;
   }
-  dm->naux_ld = round_up(naux, 4);
+  dm->naux_ld = round_up(naux, 32);
   const int nl = dm->naux_ld;
-  dm->kb_total = ((int64_t)m.ldx * nl + 31) / 32;
+  dm->kb_total = (int64_t)m.ldx * (nl / 32);
   int nch = std::max(1, (2 * m.grid + m.ntri - 1) / m.ntri);
   nch = (int)std::min<int64_t>(nch, dm->kb_total);
   dm->sy_kbpc = (dm->kb_total + nch - 1) / nch;
@@ -1319,12 +1366,14 @@ int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s) {
     BQC_TRY(make_tmap_f32(&dm->mapCh, dm->Ch.p, 2, dims, str, box));
     BQC_TRY(make_tmap_f32(&dm->mapCl, dm->Cl.p, 2, dims, str, box));
   }
-  {  // X^T as the TRMM A operand: rows (mu, i), K = Q
-    const uint64_t dims[2] = {(uint64_t)naux, (uint64_t)n * m.ldx};
-    const uint64_t str[1] = {(uint64_t)nl * 4};
-    const uint32_t box[2] = {32, kBM};
-    BQC_TRY(make_tmap_f32(&dm->mapXAh, dm->Xh.p, 2, dims, str, box));
-    BQC_TRY(make_tmap_f32(&dm->mapXAl, dm->Xl.p, 2, dims, str, box));
+  // X^T is stored in P blocks of 32: [P block][i][mu][32] (rows r = i * N + mu)
+  const uint64_t xrows = (uint64_t)n * m.ldx;
+  {  // X^T as the TRMM A operand: rows r, K = Q in blocks
+    const uint64_t dims[3] = {32, xrows, (uint64_t)(nl / 32)};
+    const uint64_t str[2] = {32 * 4, xrows * 32 * 4};
+    const uint32_t box[3] = {32, kBM, 1};
+    BQC_TRY(make_tmap_f32(&dm->mapXAh, dm->Xh.p, 3, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapXAl, dm->Xl.p, 3, dims, str, box));
   }
   {  // L^{-1}: rows P, K = Q
     const uint64_t dims[2] = {(uint64_t)naux, (uint64_t)naux};
@@ -1333,12 +1382,12 @@ int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s) {
     BQC_TRY(make_tmap_f32(&dm->mapLh, dm->Lh.p, 2, dims, str, box));
     BQC_TRY(make_tmap_f32(&dm->mapLl, dm->Ll.p, 2, dims, str, box));
   }
-  {  // Y^T as the SYRK operand: rows mu, K = (i, P)
-    const uint64_t dims[2] = {(uint64_t)m.ldx * nl, (uint64_t)n};
-    const uint64_t str[1] = {(uint64_t)m.ldx * nl * 4};
-    const uint32_t box[2] = {32, kBM};
-    BQC_TRY(make_tmap_f32(&dm->mapYh, dm->Xh.p, 2, dims, str, box));
-    BQC_TRY(make_tmap_f32(&dm->mapYl, dm->Xl.p, 2, dims, str, box));
+  {  // Y^T as the SYRK operand: rows mu, K = (i, P block, P % 32)
+    const uint64_t dims[4] = {32, (uint64_t)n, (uint64_t)m.ldx, (uint64_t)(nl / 32)};
+    const uint64_t str[3] = {32 * 4, (uint64_t)n * 32 * 4, xrows * 32 * 4};
+    const uint32_t box[4] = {32, kBM, 1, 1};
+    BQC_TRY(make_tmap_f32(&dm->mapYh, dm->Xh.p, 4, dims, str, box));
+    BQC_TRY(make_tmap_f32(&dm->mapYl, dm->Xl.p, 4, dims, str, box));
   }
   for (int k = 0; k < 2; ++k)
     BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, 1, m.xp_smem[k], nullptr, nullptr, nullptr, nullptr,
@@ -1375,8 +1424,8 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
   const int k = split == 3 ? 1 : 0;
   for (int qs = 0; qs < nq; qs += dm->bs) {
     const int nv = std::min(dm->bs, nq - qs);
-    const int64_t tot = (int64_t)n * dm->bs * m.ld;
-    k_expand_raw_mu<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+    const int nt = (m.ld + 31) / 32;
+    k_expand_raw_mu_t<<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)dm->bs), 256, 0, s>>>(
         raw, df->npair, n, m.ld, dm->bs, qs, nv, dm->Rh.as<float>(),
         split == 3 ? dm->Rl.as<float>() : nullptr);
     BQC_LAUNCH_CHECK();
@@ -1396,7 +1445,7 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
     p.bk = dm->bs;
     p.q0 = q0 + qs;
     p.bkv = nv;
-    p.naux_ld = dm->naux_ld;
+    p.xrows = (int64_t)n * m.ldx;
     const int grid = (int)std::min<int64_t>(m.grid, p.tiles);
     BQC_TRY(dispatch_xn(m.xn, split, 1, m.xp_smem[k], &p, &dm->mapRh, &dm->mapRl, &dm->mapCh,
                         &dm->mapCl, grid, s));
@@ -1413,7 +1462,6 @@ int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
   TrmmParams t;
   t.rows = (int64_t)n * m.ldx;
   t.naux = naux;
-  t.ld = dm->naux_ld;
   t.ntp = dm->ntp;
   t.stages = dm->tr_stages[k];
   t.mtiles = (t.rows + kBM - 1) / kBM;
@@ -1440,6 +1488,7 @@ int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
   q.part = dm->Kpart.as<double>();
   q.flag = df->ctx->flag;
   q.mode2d = 1;
+  q.npb = dm->naux_ld / 32;
   q.kb_total = dm->kb_total;
   q.kb_per_chunk = dm->sy_kbpc;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
