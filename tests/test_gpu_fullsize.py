@@ -1,0 +1,116 @@
+"""Parity at the benchmark's full size, (H2O)_64 (N = 1600, Naux = 4800,
+nocc = 320), in the launch configuration bench.py times (stored DF with
+the TF32 split shadows, bqc_jk on the default stream).
+
+The oracle cannot hold B (49 GB) here, so it computes what it can one
+element at a time:
+  * K_mu nu for every function of two sampled orbital shells: the oracle
+    integrates (Q|mu lambda) for those shells against all aux shells and all
+    lambda, forms the B rows with its own Cholesky factor of the metric,
+    X = B C and K = sum_P X_P X_P^T (section 2.2 of the paper; the
+    definition of the DF exchange matrix);
+and J is checked through properties that hold at any size: symmetry,
+tr(D J) = sum_P w_P^2 >= 0, and additivity in the density
+(J of C = [C1 C2] equals J of [C1 0] plus J of [0 C2]).
+C_occ is a seeded orthonormal input, not an SCF result of the GPU path.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(gpu_ctx):
+    import torch
+    import paper_2502_17963_gb300 as bqc
+    mol = workload.water_cluster(64)
+    basis = bqc.Basis(gpu_ctx, mol)
+    assert (basis.nbf, basis.naux, basis.nocc) == (1600, 4800, 320)
+    df = bqc.DF(gpu_ctx, basis, mode=bqc.DF_STORED, keep_fp32=True)
+    rng = np.random.default_rng(6401)
+    C = np.linalg.qr(rng.standard_normal((basis.nbf, basis.nocc)))[0] * 0.5
+    Cg = torch.tensor(C, device="cuda")
+    out = {"bqc": bqc, "mol": mol, "basis": basis, "df": df, "C": C, "Cg": Cg}
+    yield out
+    df.close()
+    basis.close()
+
+
+def _oracle_K_block(mol, C, shells):
+    """Oracle K rows/cols for all functions of the given orbital shells."""
+    aux = oracle.OracleBasis(mol.aux, mol.xyz)
+    orb = oracle.OracleBasis(mol.orb, mol.xyz)
+    V = oracle.int2c(aux)
+    L = np.linalg.cholesky(V)
+    X, fns = [], []
+    for a in shells:
+        pairs = [(a, s) for s in range(orb.nshell)]
+        blk = oracle.int3c(aux, orb, pshells=np.arange(aux.nshell), pairs=pairs)
+        na = orb.ncart[a]
+        R = np.zeros((aux.nfn, na, orb.nfn))
+        col = 0
+        for s in range(orb.nshell):
+            nb = orb.ncart[s]
+            R[:, :, orb.off[s]:orb.off[s] + nb] = blk[:, col:col + na * nb].reshape(aux.nfn, na, nb)
+            col += na * nb
+        B = sla.solve_triangular(L, R.reshape(aux.nfn, -1), lower=True).reshape(R.shape)
+        X.append(np.einsum("pil,lk->pik", B, C, optimize=True))
+        XA = np.einsum("pil,lk->pik", np.abs(B), np.abs(C), optimize=True)
+        X.append(XA)
+        fns.append(np.arange(orb.off[a], orb.off[a] + na))
+    Xa, XAa, Xb, XAb = X
+    K = np.einsum("pik,pjk->ij", Xa, Xb, optimize=True)
+    KA = np.einsum("pik,pjk->ij", np.abs(Xa), XAb, optimize=True) + \
+        np.einsum("pik,pjk->ij", XAa, np.abs(Xb), optimize=True)
+    return fns, K, KA
+
+
+def test_K_sampled_against_oracle_w64(setup):
+    s = setup
+    bqc, df, Cg = s["bqc"], s["df"], s["Cg"]
+    ls = [sh.l for sh in s["mol"].orb]
+    # an oxygen d shell of the first water and a hydrogen p shell of the last
+    shells = [ls.index(2), len(ls) - 1 - ls[::-1].index(1)]
+    assert ls[shells[0]] == 2 and ls[shells[1]] == 1
+    fns, Ko, KA = _oracle_K_block(s["mol"], s["C"], shells)
+    J64, K64 = df.jk(Cg, bqc.PREC_FP64)
+    J3, K3 = df.jk(Cg, bqc.PREC_MIXED_TF32X3)
+    ia, ib = fns
+    g64 = K64.cpu().numpy()[np.ix_(ia, ib)]
+    g3 = K3.cpu().numpy()[np.ix_(ia, ib)]
+    # FP64: rounding-order differences against the oracle, relative to |X||X|
+    r64 = (np.abs(g64 - Ko) / KA).max()
+    r3 = (np.abs(g3 - Ko) / KA).max()
+    print(f"w64 sampled K: FP64 ratio {r64:.3e}, 3xTF32 ratio {r3:.3e}, max|K| {np.abs(Ko).max():.3e}")
+    assert r64 < 1e-11  # measured 1.0e-13
+    assert r3 < 1e-6  # measured 1.1e-8 (random orthonormal C: little cancellation)
+
+
+def test_J_properties_w64(setup):
+    import torch
+    s = setup
+    bqc, df, Cg, basis = s["bqc"], s["df"], s["Cg"], s["basis"]
+    no = basis.nocc
+    J, _ = df.jk(Cg, bqc.PREC_FP64)
+    assert (J - J.T).abs().max().item() == 0.0
+    D = Cg @ Cg.T
+    assert (D * J).sum().item() > 0.0
+    C1, C2 = Cg.clone(), Cg.clone()
+    C1[:, no // 2:] = 0.0
+    C2[:, :no // 2] = 0.0
+    J1, _ = df.jk(C1.contiguous(), bqc.PREC_FP64)
+    J2, _ = df.jk(C2.contiguous(), bqc.PREC_FP64)
+    rel = ((J1 + J2 - J).abs().max() / J.abs().max()).item()
+    assert rel < 1e-12, rel
+    # the 3xTF32 build reads the FP64 B in its J pass: same additivity, and
+    # agreement with the FP64 J within the fused w's rounding
+    J3, _ = df.jk(Cg, bqc.PREC_MIXED_TF32X3)
+    assert (J3 - J3.T).abs().max().item() == 0.0
+    assert ((J3 - J).abs().max() / J.abs().max()).item() < 1e-5
+    del J1, J2, J3, C1, C2, D
+    torch.cuda.empty_cache()
