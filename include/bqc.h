@@ -150,7 +150,9 @@ typedef struct {
  * in-place B = L^{-1}(Q|mu nu) in FP64 (packed), plus the TF32 full-square
  * shadow when keep_fp32.  DIRECT: metric, Cholesky and screening data only;
  * (Q|mu nu) is regenerated in aux blocks at each bqc_jk ("on-the-fly",
- * "slice-by-slice", Sec. 2.2).  Work on `stream`; returns after the build has
+ * "slice-by-slice", Sec. 2.2); with keep_fp32 its tensor-core sub-blocks are
+ * sized from the device memory free at build time (memory held by a caching
+ * allocator counts as used).  Work on `stream`; returns after the build has
  * been enqueued and its workspaces allocated (synchronises the stream once to
  * size the screened work lists).  opts may be NULL for defaults. */
 int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,

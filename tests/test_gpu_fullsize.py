@@ -114,3 +114,23 @@ def test_J_properties_w64(setup):
     assert ((J3 - J).abs().max() / J.abs().max()).item() < 1e-5
     del J1, J2, J3, C1, C2, D
     torch.cuda.empty_cache()
+
+
+def test_direct_equals_stored_w64(setup):
+    """Direct DF (integrals regenerated per aux block of 1024, as at
+    (H2O)_128) against stored DF at (H2O)_64, FP64: the two paths share only
+    the integral kernel (J from c = V^-1 gamma and the raw integrals vs from
+    B; K from L^-1 X vs from B C)."""
+    import torch
+    s = setup
+    bqc, Cg, basis = s["bqc"], s["Cg"], s["basis"]
+    J, K = s["df"].jk(Cg, bqc.PREC_FP64)
+    dd = bqc.DF(s["df"].ctx, basis, mode=bqc.DF_DIRECT, aux_block=1024, keep_fp32=False)
+    Jd, Kd = dd.jk(Cg, bqc.PREC_FP64)
+    dJ = (Jd - J).abs().max().item()
+    dK = (Kd - K).abs().max().item()
+    print(f"w64 direct vs stored FP64: max|dJ| {dJ:.3e}, max|dK| {dK:.3e}")
+    assert dJ < 1e-9 and dK < 1e-9
+    dd.close()
+    del Jd, Kd
+    torch.cuda.empty_cache()
