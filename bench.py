@@ -178,7 +178,9 @@ def config(mol, prec):
     naux = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.aux)
     return {"workload": f"{mol.name} DF-RHF Fock build, stored B, N={n}, Naux={naux}, "
                         f"nocc={mol.nocc}", "prec": prec, "seed": len(mol.Z) // 3,
-            "l2": "inputs larger than L2 (TF32 B shadow 49 GB streamed per step)",
+            "l2": f"inputs larger than L2 (per step: {naux * n * ((n + 3) // 4 * 4) * 8 / 1e9:.1f} GB "
+                  f"of split TF32 B shadows read by the X pass, {naux * n * (n + 1) / 2 * 8 / 1e9:.1f} GB "
+                  "of FP64 B by the J pass)",
             "parallelism": "replicas"}
 
 

@@ -112,7 +112,8 @@ __device__ __forceinline__ float tf32r(float x) {
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr int kGroupKb = 4;   // k-blocks (of 32) per TMEM chain: X pass (contraction N)
-constexpr int kGroupKbS = 2;  // SYRK and TRMM (contractions of Naux x nocc and Naux)
+constexpr int kGroupKbS = 4;  // SYRK (contraction Naux x nocc)
+constexpr int kGroupKbT = 2;  // TRMM (contraction Naux)
 
 struct XpassParams {
   int64_t rows;      // Naux * N  (M of the GEMM)
@@ -682,14 +683,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = blockIdx.x; t < p.mtiles && ok; t += gridDim.x) {
         for (int pt = p.ntp - 1; pt >= 0 && ok; --pt) {
           const int nkb = kblocks_of(pt);
-          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKbS, ++g) {
+          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKbT, ++g) {
             const int b = (int)(g & 1);
             if (g >= 2)
               ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 34);
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tbase + b * kBM;
-            const int kb1 = min(nkb, kb0 + kGroupKbS);
+            const int kb1 = min(nkb, kb0 + kGroupKbT);
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
               const int st = (int)(kg % p.stages);
               ok = mbar_wait(full0 + 8 * st, (uint32_t)((kg / p.stages) & 1), p.flag, 32);
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float acc[HALF];
 #pragma unroll
         for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
-        for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKbS, ++g) {
+        for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKbT, ++g) {
           const int b = (int)(g & 1);
           if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 33);
           __syncwarp();
