@@ -59,6 +59,20 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The slowest rank's time: all-reduce(MAX) of one float."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, seconds: float) -> float:
+    """Fock builds per second of the whole job: every rank (an independent
+    replica) ran `steps` builds within the slowest rank's `seconds`."""
+    return world * steps / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -368,12 +382,10 @@ def main():
     clk = clocks.stop()
     df.timing(False)
     if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
         dist.barrier()
     ms_per_step = elapsed_ms / args.steps
-    value = world * args.steps / (elapsed_ms * 1e-3)
+    value = whole_job_rate(world, args.steps, elapsed_ms * 1e-3)
     ph = np.array(phases)
     ph_mean = ph.mean(axis=0).tolist()
 
@@ -433,10 +445,8 @@ def main():
             df.jk_host(Cn, MIX, Jn, Kn)
         dt = time.perf_counter() - t0
         if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * args.steps / dt, "unit": UNIT,
+            dt = max_over_ranks(dt, dist, "cuda")
+        e2e = {"value": whole_job_rate(world, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": n * no * 8, "d2h_bytes_per_step": 2 * n * n * 8}
 
     if rank != 0:
