@@ -113,6 +113,13 @@ def test_staged_scf_energy(gpu_ctx, bqc, name):
     I = oracle.system_integrals(mol)
     B, _ = oracle.df_tensor(I["aux"], I["orb"])
     ro = oracle.rhf(I["S"], I["H"], lambda C: oracle.jk_df(B, C), mol.nocc, I["enuc"])
-    print(name, r)
+    print(name, {k: v for k, v in r.items() if k != "history"})
     assert r["converged"] and r["iterations_mixed"] > 0
     assert abs(r["energy"] - ro.energy) < 1e-8
+    # one history entry per Fock build: the mixed ones (the last of them is
+    # redone in FP64 at the switch), then FP64 to convergence
+    h, m = r["history"], r["iterations_mixed"]
+    assert len(h) == r["iterations"] + 1
+    assert all(p == bqc.PREC_MIXED_TF32X3 for p, _, _ in h[:m])
+    assert all(p == bqc.PREC_FP64 for p, _, _ in h[m:])
+    assert h[-1][1] == r["diis_err"] < 1e-8 and h[-1][2] == r["energy"]
