@@ -2,9 +2,9 @@
  * bqc.h - C ABI of the GB300 density-fitted RHF Fock-build library.
  *
  * The method is the mean-field stage of arXiv 2502.17963 (ByteQC), Sec. 2.2:
- * three-index "Cholesky-decomposition ERIs" built from an auxiliary basis,
- * stored once when they fit ("ERIs are only affected by the basis set and the
- * atomic structure"), regenerated on the fly in auxiliary slices when they do
+ * three-index Cholesky-decomposed ERIs built from an auxiliary basis, stored
+ * once when they fit (they depend only on the basis and the geometry, not on
+ * the SCF iterate), regenerated in slices of the auxiliary basis when they do
  * not, and contracted into the Coulomb and exchange matrices inside the SCF.
  * The paper prints no equations for this path; the operations below are the
  * textbook ones (Szabo & Ostlund Ch. 3; Helgaker, Jorgensen & Olsen Ch. 9).
@@ -53,7 +53,7 @@ enum {
   BQC_E_TIMEOUT = -6,       /* a bounded device or host wait ran out        */
   BQC_E_DEVICE_FLAG = -7,   /* a kernel's own bounds check tripped          */
   BQC_E_NOT_READY = -8,     /* serving: result not available yet            */
-  BQC_E_UNSUPPORTED = -9    /* angular momentum / size beyond this build    */
+  BQC_E_UNSUPPORTED = -9    /* angular momentum / size the library lacks    */
 };
 
 /* Precision of the Fock build (the X = B C and K contractions, the B.D
@@ -98,9 +98,10 @@ typedef struct {
   const double *coefs;
 } bqc_shell;
 
-/* Load a molecule and its orbital and auxiliary bases (Sec. 2.2: DF needs
- * an "auxiliary artificial molecule").  Z: natom nuclear charges; xyz_bohr:
- * natom x 3.  Orbital l <= 2 and auxiliary l <= 3 in this build (up to the
+/* Load a molecule and its orbital and auxiliary bases (Sec. 2.2: DF expands
+ * orbital products in an auxiliary basis on the same atoms).  Z: natom
+ * nuclear charges; xyz_bohr: natom x 3.  Orbital l <= 2 and auxiliary
+ * l <= 3 (compiled limits; up to the
  * (f|dd) class), else BQC_E_UNSUPPORTED; sum Z must be even (closed shell),
  * else BQC_E_INVALID.  Copies everything; the shell setup (normalisation,
  * pair classes) runs here. */
@@ -149,8 +150,9 @@ typedef struct {
 /* Build the DF machinery (Sec. 2.2).  STORED: metric, Cholesky, raw (Q|mu nu),
  * in-place B = L^{-1}(Q|mu nu) in FP64 (packed), plus the TF32 full-square
  * shadow when keep_fp32.  DIRECT: metric, Cholesky and screening data only;
- * (Q|mu nu) is regenerated in aux blocks at each bqc_jk ("on-the-fly",
- * "slice-by-slice", Sec. 2.2); with keep_fp32 its tensor-core sub-blocks are
+ * (Q|mu nu) is regenerated in aux blocks at each bqc_jk (Sec. 2.2: computed
+ * again slice by slice when too large to keep); with keep_fp32 its tensor-core
+ * sub-blocks are
  * sized from the device memory free at build time (memory held by a caching
  * allocator counts as used).  Work on `stream`; returns after the build has
  * been enqueued and its workspaces allocated (synchronises the stream once to

@@ -1,12 +1,13 @@
 // Density-fitting tensor and the J/K build (Sec. 2.2).
 //
-// Stored mode ("ERIs ... only need to be calculated once and stored"):
+// Stored mode (the three-index tensor depends only on basis and geometry, so
+// it is computed once and kept):
 //   V = (P|Q) -> L (Cholesky) -> raw (Q|mu nu) packed lower triangle in FP64
 //   -> B = L^{-1} raw in place -> optional TF32-rounded full-square shadow.
 // Each Fock build then makes two passes over B, as the paper notes for the
 // Coulomb matrix: the X pass (X_P = B_P C_occ, with w_P = <X_P, C_occ>) and
 // the J pass (J = sum_P w_P B_P); K = sum_P X_P X_P^T.
-// Direct mode (on-the-fly, slice-by-slice): see direct.cu.
+// Direct mode (regenerated per aux block at every build): see direct.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,5 +1,5 @@
 // Gaussian integrals on the GPU: Boys function, Obara-Saika / Head-Gordon-Pople
-// recursions for the three-centre (P|mu nu) "Cholesky-decomposition ERIs" of
+// recursions for the three-centre (P|mu nu) Cholesky-decomposed ERIs (CD-ERIs) of
 // the density-fitted mean field (Sec. 2.2), the Coulomb metric (P|Q), the
 // Schwarz diagonals (mu nu|mu nu) and the one-electron matrices.
 //

@@ -1,7 +1,7 @@
 // FP64 dense kernels of the DF pipeline: a DFMA GEMM (the plain-FP64
 // contractions and the metric solve), blocked Cholesky of the Coulomb metric
 // V = L L^T, and the in-place triangular solve B = L^{-1} (Q|mu nu) that
-// turns raw three-centre integrals into the "Cholesky-decomposition ERIs" of
+// turns raw three-centre integrals into the Cholesky-decomposed ERIs (CD-ERIs) of
 // Sec. 2.2.
 //
 // On GB300 FP64 runs at ~1.2 TFLOP/s (about 2 DFMA per clock per SM), so a
