@@ -8,7 +8,7 @@ What it computes (the paper names these techniques in Sec. 2.2 without
 equations; the formulas are textbook, cited per function):
   * Gaussian integrals by McMurchie-Davidson (``md_ints.c``);
   * the density-fitting tensor B = L^{-1} (Q|mu nu) with V = L L^T, the
-    "Cholesky-decomposition ERIs" of Sec. 2.2;
+    Cholesky-decomposed ERIs (CD-ERIs) of Sec. 2.2;
   * J and K from B and the occupied orbitals, F = H + 2J - K;
   * the closed-shell SCF with canonical orthogonalisation, core guess and
     Pulay DIIS (Szabo & Ostlund, Sec. 3.4; Pulay 1982).

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-The paper (Sec. 2.2) builds the mean field from "Cholesky-decomposition ERIs":
+The paper (Sec. 2.2) builds the mean field from Cholesky-decomposed ERIs:
 with the Coulomb metric V = (P|Q) = L L^T, B_P,mu nu = sum_Q (L^{-1})_PQ (Q|mu nu)
 so that (mu nu|lambda sigma) ~ sum_P B_P,mu nu B_P,lambda sigma.  With
 D = C_occ C_occ^T (no factor 2), J = sum_P B_P (B_P : D) and
