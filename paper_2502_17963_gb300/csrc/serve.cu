@@ -30,8 +30,11 @@ namespace bqc {
 
 // ------------------------------------------------------------- arena ----
 
-// First-fit sub-allocator over one device allocation; blocks are 256-byte
-// aligned and neighbouring free blocks are merged on release.
+// Sub-allocator over one device allocation; blocks are 256-byte aligned and
+// neighbouring free blocks are merged on release.  Small blocks are placed
+// first-fit from the bottom, large ones (>= kLarge) best-fit at the top end
+// of their free block, so that the many small buffers of concurrent solves
+// do not split the space the multi-GB DF tensors need.
 struct Arena {
   char *base = nullptr;
   size_t size = 0;
@@ -54,20 +57,35 @@ struct Arena {
   ~Arena() {
     if (base) cudaFree(base);
   }
+  static constexpr size_t kLarge = (size_t)256 << 20;
   void *alloc(size_t bytes) {
     bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
     std::lock_guard<std::mutex> g(mu);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      const size_t off = it->first, rest = it->second - bytes;
-      free_.erase(it);
-      if (rest) free_[off + bytes] = rest;
-      used_[off] = bytes;
-      in_use += bytes;
-      peak = std::max(peak, in_use);
-      return base + off;
+    auto pick = free_.end();
+    if (bytes < kLarge) {
+      for (auto it = free_.begin(); it != free_.end(); ++it)
+        if (it->second >= bytes) {
+          pick = it;
+          break;
+        }
+    } else {
+      for (auto it = free_.begin(); it != free_.end(); ++it)
+        if (it->second >= bytes && (pick == free_.end() || it->second < pick->second)) pick = it;
     }
-    return nullptr;
+    if (pick == free_.end()) return nullptr;
+    const size_t off0 = pick->first, len = pick->second, rest = len - bytes;
+    free_.erase(pick);
+    size_t off = off0;
+    if (bytes < kLarge) {
+      if (rest) free_[off0 + bytes] = rest;
+    } else {
+      off = off0 + rest;  // top end of the block
+      if (rest) free_[off0] = rest;
+    }
+    used_[off] = bytes;
+    in_use += bytes;
+    peak = std::max(peak, in_use);
+    return base + off;
   }
   void release(void *p) {
     if (!p) return;
@@ -110,6 +128,10 @@ struct Request {
   int nbf = 0, naux = 0, nocc = 0;
   size_t footprint = 0;
   int skipped = 0;  // times a later request was admitted ahead of this one
+  int retries = 0;  // re-admissions after an allocation failure
+  bool wait_for_release = false;  // requeued: wait until another solve ends
+  uint64_t release_mark = 0;      // srv->releases when it was requeued
+  double t_submit = 0.0;
   bool done = false;
   bqc_serve_result res{};
 };
@@ -133,6 +155,7 @@ struct bqc_server {
   int pending = 0;
   bool stop = false;
   int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range
+  uint64_t releases = 0;                  // solves finished (their memory freed)
   std::chrono::steady_clock::time_point t0;
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -210,7 +233,10 @@ static int request_priority(const bqc_server *srv, int nbf) {
 // count grows; once it reaches max_skips nothing passes the head any more.
 static Request *pick_request(bqc_server *srv) {
   if (srv->queue.empty()) return nullptr;
-  auto fits = [&](const Request *r) { return srv->ledger + r->footprint <= srv->budget; };
+  auto fits = [&](const Request *r) {
+    if (r->wait_for_release && srv->releases <= r->release_mark) return false;
+    return srv->ledger + r->footprint <= srv->budget;
+  };
   Request *h = srv->reqs[srv->queue.front()].get();
   if (fits(h)) {
     srv->queue.pop_front();
@@ -253,15 +279,32 @@ static void worker_main(bqc_server *srv) {
     } else {
       r->res.status = BQC_E_CUDA;
     }
+    bool requeued = false;
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       srv->ledger -= r->footprint;
-      r->res.t_done = srv->now();
-      r->done = true;
-      --srv->pending;
+      // The ledger admitted it, so an allocation failure means the free space
+      // was split by the solves in flight: retry at the head of the queue once
+      // some of them have finished (a bounded number of times).
+      if (r->res.status == BQC_E_OOM && srv->ledger > 0 && r->retries < 4) {
+        ++r->retries;
+        r->res = bqc_serve_result{};
+        r->res.status = BQC_E_NOT_READY;
+        r->res.nbf = r->nbf;
+        r->res.t_submit = r->t_submit;
+        r->wait_for_release = true;
+        r->release_mark = srv->releases;
+        srv->queue.push_front(r->id);
+        requeued = true;
+      } else {
+        r->res.t_done = srv->now();
+        r->done = true;
+        --srv->pending;
+        ++srv->releases;
+      }
     }
     srv->cv_work.notify_all();
-    srv->cv_done.notify_all();
+    if (!requeued) srv->cv_done.notify_all();
   }
   for (cudaStream_t s : streams)
     if (s) cudaStreamDestroy(s);
@@ -354,6 +397,7 @@ int bqc_serve_submit(bqc_server *srv, const bqc_request *q, uint64_t *ticket) {
   r->res.status = BQC_E_NOT_READY;
   r->res.nbf = r->nbf;
   r->res.t_submit = srv->now();
+  r->t_submit = r->res.t_submit;
   *ticket = r->id;
   srv->queue.push_back(r->id);
   ++srv->pending;
