@@ -773,7 +773,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // -------------------------------------------------------------- J pass ---
 
-// J[mu][nu <= mu] = sum_P w_P B[P][mu][nu] into packed FP64, B = Bh (+ Bl).
+// J[mu][nu <= mu] = sum_P w_P Bh[P][mu][nu] into packed FP64 from the TF32
+// shadow (the single-pass TF32 build; the 3xTF32 build reads the FP64 B).
 // Block b owns rows b and N-1-b (balanced work); a thread owns 4 consecutive
 // columns of one row and streams every P (float4 loads, FP32 partial sums
 // over 64 P, folded into FP64).
@@ -781,9 +782,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // on each SM: the J pass streams HBM while the SYRK keeps the tensor cores busy.
 constexpr int kJThreads = 128;
 
-template <int SPLIT>
 __global__ void __launch_bounds__(kJThreads) k_jpass_tf32(const float *__restrict__ Bh,
-                                                          const float *__restrict__ Bl,
                                                           const float *__restrict__ w32, int naux,
                                                           int n, int ld, double *__restrict__ Jp) {
   const int b = blockIdx.x;
@@ -803,14 +802,7 @@ __global__ void __launch_bounds__(kJThreads) k_jpass_tf32(const float *__restric
 #pragma unroll 8
       for (int P = P0; P < P1; ++P) {
         const float wp = __ldg(w32 + P);
-        float4 v = __ldg(reinterpret_cast<const float4 *>(Bh + off + P * nn));
-        if (SPLIT == 3) {
-          const float4 l = __ldg(reinterpret_cast<const float4 *>(Bl + off + P * nn));
-          v.x += l.x;
-          v.y += l.y;
-          v.z += l.z;
-          v.w += l.w;
-        }
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(Bh + off + P * nn));
         a.x = fmaf(wp, v.x, a.x);
         a.y = fmaf(wp, v.y, a.y);
         a.z = fmaf(wp, v.z, a.z);
@@ -1184,9 +1176,8 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   } else {
     const dim3 jgrid((unsigned)((n + 1) / 2),
                      (unsigned)(((n - 1) / 4 + 2 + kJThreads - 1) / kJThreads));
-    k_jpass_tf32<1><<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), nullptr,
-                                                 ms->w32.as<float>(), naux, n, m.ld,
-                                                 df->Jp.as<double>());
+    k_jpass_tf32<<<jgrid, kJThreads, 0, js>>>(df->B32.as<float>(), ms->w32.as<float>(), naux,
+                                              n, m.ld, df->Jp.as<double>());
     BQC_LAUNCH_CHECK();
     k_unpack_sym2<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, js>>>(df->Jp.as<double>(),
                                                                              n, J);
