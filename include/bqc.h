@@ -222,7 +222,9 @@ int bqc_df_phase_ms(bqc_df *df, float *ms, int n);
 
 typedef struct {
   double diis_tol;     /* max |X^T (FDS - SDF) X| to converge (default 1e-8)   */
-  double energy_tol;   /* |E - E_prev| to converge (default 1e-10)             */
+  double energy_tol;   /* |E - E_prev| to converge (default 1e-10); the bar is
+                          max(energy_tol, eps_64 * N * |E|), the energy's own
+                          rounding noise, which is larger from N ~ 800 */
   double stage_tol;    /* mixed -> FP64 switch when DIIS error below (1e-5)   */
   int max_iter;        /* default 100                                         */
   int diis_space;      /* default 8                                           */

@@ -123,7 +123,8 @@ def rhf(S: np.ndarray, H: np.ndarray, jk: Callable[[np.ndarray], Tuple[np.ndarra
 
     Each iteration: J, K from the current C_occ; F = H + 2J - K;
     E = sum D (H + F) + E_nn; e = X^T (F D S - S D F) X; converged when
-    max|e| < tol and |E - E_prev| < etol; else DIIS over the last diis_space
+    max|e| < tol and |E - E_prev| < max(etol, eps * N * |E|) (the energy's own
+    rounding noise, a sum over N^2 products); else DIIS over the last diis_space
     (F, e) pairs once two are stored, then diagonalise X^T F X.
     """
     X = canonical_orthogonaliser(S, orth_thresh)
@@ -152,7 +153,8 @@ def rhf(S: np.ndarray, H: np.ndarray, jk: Callable[[np.ndarray], Tuple[np.ndarra
         err = X.T @ (F @ D @ S - S @ D @ F) @ X
         emax = float(np.max(np.abs(err)))
         hist.append((E, emax))
-        if emax < tol and E_prev is not None and abs(E - E_prev) < etol:
+        enoise = np.finfo(np.float64).eps * S.shape[0] * abs(E)
+        if emax < tol and E_prev is not None and abs(E - E_prev) < max(etol, enoise):
             converged = True
             break
         E_prev = E

@@ -4,12 +4,13 @@
 // oracle's): canonical orthogonalisation X = U s^{-1/2} over eigenvalues of S
 // above orth_thresh; core-Hamiltonian guess; each iteration builds J, K from
 // C_occ, F = H + 2J - K, E = sum D (H + F) + E_nn, e = X^T (F D S - S D F) X;
-// converged when max|e| < diis_tol and |E - E_prev| < energy_tol; otherwise
-// DIIS over the last diis_space (F, e) pairs once two are stored, and
-// diagonalise X^T F X.  Precision staging: a MIXED first stage switches to
-// FP64 (DIIS history cleared) when max|e| < stage_tol, or when the mixed
-// stage stops improving (no new minimum of max|e| for 4 iterations), since
-// a TF32 Fock matrix carries errors near that size.
+// converged when max|e| < diis_tol and |E - E_prev| < max(energy_tol,
+// eps_64 * N * |E|) (the second term is the rounding noise of the energy
+// itself, a sum over N^2 products, which exceeds 1e-10 Eh from N of about
+// 800); otherwise DIIS over the last diis_space (F, e) pairs once two are
+// stored, and diagonalise X^T F X.  Precision staging: a MIXED first stage
+// switches to FP64 (DIIS history cleared) at stage_tol or at the mixed
+// stage's error floor (see the rule at the switch below).
 //
 // Linear algebra here (eigh, small GEMMs, dots) uses cuSOLVER / cuBLAS in
 // FP64; everything is column-major; symmetric matrices need no conversion.
@@ -18,6 +19,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <vector>
 
@@ -310,7 +312,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
       h[2] = E;
     }
     if (stage == BQC_PREC_FP64 && emax < o.diis_tol && have_prev &&
-        std::fabs(E - Eprev) < o.energy_tol) {
+        std::fabs(E - Eprev) < std::max(o.energy_tol, DBL_EPSILON * n * std::fabs(E))) {
       converged = true;
       break;
     }
