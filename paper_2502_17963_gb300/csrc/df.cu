@@ -334,7 +334,7 @@ int bqc_df_phase_ms(bqc_df *df, float *ms, int n) {
   BQC_CUDA_TRY(cudaEventElapsedTime(&t[0], df->ev[1], df->ev[2]));
   BQC_CUDA_TRY(cudaEventElapsedTime(&t[3], df->ev[0], df->ev[1]));
   if (df->mode == BQC_DF_STORED && df->side && df->last_mixed) {
-    // mixed stored build: J (side stream, ev[j_from] -> ev5) overlaps the
+    // mixed stored build: J (side stream, ev[j_from] -> ev5) runs beside the
     // tensor-core passes; K is the SYRK (ev2 -> ev3)
     BQC_CUDA_TRY(cudaEventElapsedTime(&t[1], df->ev[df->j_from], df->ev[5]));
     BQC_CUDA_TRY(cudaEventElapsedTime(&t[2], df->ev[2], df->ev[3]));

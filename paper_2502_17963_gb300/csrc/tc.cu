@@ -1,18 +1,19 @@
 // Mixed-precision Fock build on the 5th-generation tensor cores (tcgen05).
 //
 // The two passes over the CD-ERIs that the paper describes for the Coulomb
-// and exchange matrices (Sec. 2.2) become, with B held as a TF32-rounded
-// full-square shadow B32[P][mu][nu]:
-//   X pass  X[(P,mu)][i] = sum_nu B32[(P,mu)][nu] C[nu][i]       (one GEMM,
+// and exchange matrices (Sec. 2.2) become, with B held as TF32 split
+// full-square shadows Bh/Bl[P][mu][nu]:
+//   X pass  X[(P,mu)][i] = sum_nu B[(P,mu)][nu] C[nu][i]         (one GEMM,
 //           M = Naux*N, N = nocc, K = N) with the Coulomb contraction
 //           w_P = sum_{mu,i} X[(P,mu)][i] C[mu][i] fused into the epilogue;
 //   SYRK    K[mu][nu] = sum_{P,i} X[P][mu][i] X[P][nu][i], lower tiles only,
-//           split over aux chunks whose FP32 partials are summed in FP64;
-//   J pass  J[mu][nu<=mu] = sum_P w_P B32[P][mu][nu]  (HBM-bound stream).
+//           split over aux chunks whose partials are summed in FP64;
+//   J pass  J = sum_P w_P B_P over the packed FP64 B (df.cu, 3xTF32) or the
+//           TF32 shadow (single-pass TF32), on a side stream beside the SYRK.
 // Tensor-core kernels: TMA (128-byte swizzle) -> shared memory ring ->
 // tcgen05.mma kind::tf32 issued by one thread -> FP32 accumulators in TMEM
-// -> tcgen05.ld epilogue.  Warp 0 produces, warp 1 issues MMAs, all four
-// warps drain TMEM.  Every mbarrier wait is bounded; on timeout the kernel
+// -> tcgen05.ld epilogue.  Warp 0 produces, warp 1 issues MMAs, eight warps
+// drain TMEM.  Every mbarrier wait is bounded; on timeout the kernel
 // records an error code in the context's device flag and skips its work.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -779,7 +780,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // columns of one row and streams every P (float4 loads, FP32 partial sums
 // over 64 P, folded into FP64).
 // Blocks are small (kJThreads) so that one fits beside a persistent SYRK CTA
-// on each SM: the J pass streams HBM while the SYRK keeps the tensor cores busy.
+// on each SM: the J pass streams HBM while the SYRK keeps the tensor cores
+// busy.
 constexpr int kJThreads = 128;
 
 __global__ void __launch_bounds__(kJThreads) k_jpass_tf32(const float *__restrict__ Bh,
