@@ -193,7 +193,10 @@ int bqc_jk(bqc_df *df, const double *C_occ_dev, int nocc, int prec, double *J_de
  * sizes return BQC_E_INVALID (bqc_last_error names the size) before any work.
  * The first call on a device looks up that array's device address (one-time
  * set-up, with the device current); make that first call before any stream
- * capture.  All calls on a device share the array: calls whose work overlaps
+ * capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset() of a device it is stale, so do not call this entry
+ * point on that device again in the same process.  The limit admits the
+ * single water up to (H2O)_7 of the cluster workloads.  All calls on a device share the array: calls whose work overlaps
  * on the GPU (different streams, or host threads without ordering) race and
  * must be serialised by the caller.  Async. */
 #define BQC_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -201,7 +204,8 @@ int bqc_jk_fp64_noalloc(const double *B_dev, int naux, int nbf, const double *C_
                         int nocc, double *J_dev, double *K_dev, bqc_stream_t stream);
 
 /* Same as bqc_jk with host buffers: copies C_occ in, J and K out, and
- * waits for the stream.  The end-to-end entry point. */
+ * waits for the stream.  The end-to-end entry point.  A non-finite entry of
+ * C_occ returns BQC_E_INVALID before anything is copied or launched. */
 int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, double *K,
                 bqc_stream_t stream);
 
@@ -253,7 +257,16 @@ typedef struct {
   double *history;
   int history_cap;
   int history_len;
+  /* Precision staging (output): which rule ended the mixed stage
+   * (BQC_SWITCH_NONE if the SCF ran in one precision, BQC_SWITCH_STAGE_TOL
+   * when the DIIS error fell below stage_tol, BQC_SWITCH_FLOOR when the mixed
+   * stage stopped improving above it) and the max-abs DIIS error of the last
+   * mixed iteration. */
+  int switch_rule;
+  double switch_err;
 } bqc_scf_result;
+
+enum { BQC_SWITCH_NONE = 0, BQC_SWITCH_STAGE_TOL = 1, BQC_SWITCH_FLOOR = 2 };
 
 /* Closed-shell SCF (canonical orthogonalisation, core-Hamiltonian guess,
  * Pulay DIIS on e = X^T (FDS - SDF) X, aufbau) with the Fock build of
@@ -329,6 +342,15 @@ int bqc_serve_drain(bqc_server *srv, double timeout_s);
 int bqc_serve_destroy(bqc_server *srv);
 /* Predicted device bytes of a request of this size (the admission ledger). */
 size_t bqc_serve_footprint(int nbf, int naux, int nocc);
+
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * kernel whose only thread waits on a device barrier that nothing completes,
+ * through the bounded wait every tensor-core kernel uses, and reads the
+ * context's device flag.  The wait gives up after `cycles` SM clocks
+ * (1 .. 4e9), records its code, and the kernel returns normally, so the call
+ * returns BQC_E_DEVICE_FLAG and the context stays usable.  BQC_E_INVALID for
+ * cycles out of range.  Synchronises the stream. */
+int bqc_wait_selftest(bqc_ctx *ctx, long long cycles, bqc_stream_t stream);
 
 const char *bqc_strerror(int status);
 /* Text of the last error recorded on the calling thread (file:line of the failing call). */

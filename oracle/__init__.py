@@ -20,7 +20,11 @@ none for this path).
 from .ints import OracleBasis, boys, one_electron, int2c, int3c, int4c, nuclear_repulsion  # noqa: F401
 from .scf import (  # noqa: F401
     df_tensor,
+    df_tensor_packed,
     jk_df,
+    jk_df_packed,
+    raw_3c_packed,
+    unpack_rows,
     jk_4c,
     rhf,
     RhfResult,

@@ -73,6 +73,85 @@ def jk_df(B: np.ndarray, Cocc: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     return J, K
 
 
+def raw_3c_packed(aux: OracleBasis, orb: OracleBasis) -> np.ndarray:
+    """(P|mu nu) on the packed lower triangle, (Naux, N(N+1)/2) with column
+    mu(mu+1)/2 + nu for mu >= nu; computed one orbital shell a at a time (all
+    its pairs (a, b <= a) against every aux shell), so the full square is
+    never held."""
+    N = orb.nfn
+    out = np.zeros((aux.nfn, N * (N + 1) // 2))
+    for a in range(orb.nshell):
+        pairs = [(a, b) for b in range(a + 1)]
+        blk = int3c(aux, orb, pairs=pairs)
+        na = orb.ncart[a]
+        col = 0
+        for _, b in pairs:
+            nb = orb.ncart[b]
+            t = blk[:, col:col + na * nb].reshape(-1, na, nb)
+            for i in range(na):
+                mu = orb.off[a] + i
+                for j in range(nb):
+                    nu = orb.off[b] + j
+                    if nu <= mu:
+                        out[:, mu * (mu + 1) // 2 + nu] = t[:, i, j]
+            col += na * nb
+    return out
+
+
+def df_tensor_packed(aux: OracleBasis, orb: OracleBasis, col_block: int = 32768):
+    """B = L^{-1} (Q|mu nu) on the packed lower triangle (Naux, Npair), V = L L^T.
+
+    The definition of df_tensor; B's column for one orbital pair depends only
+    on that pair's column of (Q|mu nu), so the triangular solve runs over
+    blocks of columns (the aux-blocked CPU form that large clusters need).
+    Returns (B packed, L).
+    """
+    V = int2c(aux)
+    L = np.linalg.cholesky(V)
+    B = raw_3c_packed(aux, orb)
+    for c0 in range(0, B.shape[1], col_block):
+        c1 = min(B.shape[1], c0 + col_block)
+        B[:, c0:c1] = sla.solve_triangular(L, B[:, c0:c1], lower=True)
+    return B, L
+
+
+def unpack_rows(Bp: np.ndarray, N: int) -> np.ndarray:
+    """Packed lower triangles (rows, Npair) -> symmetric full squares (rows, N, N)."""
+    out = np.zeros((Bp.shape[0], N, N))
+    il = np.tril_indices(N)
+    out[:, il[0], il[1]] = Bp
+    out[:, il[1], il[0]] = Bp
+    return out
+
+
+def jk_df_packed(Bp: np.ndarray, N: int, Cocc: np.ndarray, block: int = 64, bounds=False):
+    """jk_df over a packed B, summing the aux index P in blocks of `block`
+    (J and K are sums over P of per-P terms).  With bounds=True also returns
+    the absolute contractions JA = sum_P |w_P| |B_P| and
+    KA = sum_P |X_P| (|B_P| |C|)^T + (|B_P| |C|) |X_P|^T, the scale of the
+    rounding error of any evaluation order."""
+    J = np.zeros((N, N))
+    K = np.zeros((N, N))
+    JA = np.zeros((N, N)) if bounds else None
+    KA = np.zeros((N, N)) if bounds else None
+    Ca = np.abs(Cocc)
+    for P0 in range(0, Bp.shape[0], block):
+        Bf = unpack_rows(Bp[P0:P0 + block], N)
+        X = np.einsum("pmn,ni->pmi", Bf, Cocc, optimize=True)
+        w = np.einsum("pmi,mi->p", X, Cocc, optimize=True)
+        J += np.einsum("p,pmn->mn", w, Bf, optimize=True)
+        K += np.einsum("pmi,pni->mn", X, X, optimize=True)
+        if bounds:
+            Ba = np.abs(Bf)
+            XA = np.einsum("pmn,ni->pmi", Ba, Ca, optimize=True)
+            JA += np.einsum("p,pmn->mn", np.abs(w), Ba, optimize=True)
+            t = np.einsum("pmi,pni->mn", np.abs(X), XA, optimize=True)
+            KA += t + t.T
+    if bounds:
+        return J, K, JA, KA
+    return J, K
+
+
 def jk_4c(eri: np.ndarray, Cocc: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     """J_mn = sum (mn|ls) D_ls, K_mn = sum (ml|ns) D_ls with D = C_occ C_occ^T."""
     D = Cocc @ Cocc.T

@@ -62,7 +62,8 @@ class bqc_scf_result(ctypes.Structure):
                 ("converged", ctypes.c_int), ("iterations_mixed", ctypes.c_int),
                 ("nmo", ctypes.c_int), ("C_dev", ctypes.c_void_p), ("eps_dev", ctypes.c_void_p),
                 ("F_dev", ctypes.c_void_p), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int)]
+                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int),
+                ("switch_rule", ctypes.c_int), ("switch_err", ctypes.c_double)]
 
 
 class bqc_serve_opts(ctypes.Structure):
@@ -127,6 +128,7 @@ _SIGS = {
     "bqc_serve_drain": (ip, [vp, dp]),
     "bqc_serve_destroy": (ip, [vp]),
     "bqc_serve_footprint": (ctypes.c_size_t, [ip, ip, ip]),
+    "bqc_wait_selftest": (ip, [vp, ctypes.c_longlong, vp]),
 }
 
 
@@ -400,6 +402,8 @@ def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
         raise BqcError(st, "bqc_scf_run")
     out = dict(energy=r.energy, e_nuc=r.e_nuc, diis_err=r.diis_err, iterations=r.iterations,
                converged=bool(r.converged), iterations_mixed=r.iterations_mixed, nmo=r.nmo,
+               switch_rule={0: None, 1: "stage_tol", 2: "floor"}.get(r.switch_rule),
+               switch_err=r.switch_err if r.switch_rule else None,
                history=[(int(hist[3 * i]), hist[3 * i + 1], hist[3 * i + 2])
                         for i in range(r.history_len)])
     if keep_arrays:

@@ -35,6 +35,10 @@ const char *last_error();
     if (s__ != BQC_OK) return s__;                                           \
   } while (0)
 
+// Multiprocessor count of the current device (cached per device); grids of
+// persistent kernels and the memory plans that depend on them use it.
+int sm_count();
+
 // Launch check: reports launch-configuration errors without synchronising.
 #define BQC_LAUNCH_CHECK() BQC_CUDA_TRY(cudaPeekAtLastError())
 

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
@@ -100,7 +102,7 @@ __global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n
 // aux chunks of the J pass: enough blocks for four per SM, at least 64 P each
 int jpass_split(int64_t npair, int naux) {
   const int64_t blocks = (npair / 2 + 256) / 256;
-  int sp = (int)std::min<int64_t>(16, (4 * 152 + blocks - 1) / blocks);
+  int sp = (int)std::min<int64_t>(16, (4 * (int64_t)sm_count() + blocks - 1) / blocks);
   sp = std::max(1, std::min(sp, naux / 64));
   return sp;
 }
@@ -368,6 +370,15 @@ int bqc_jk_host(bqc_df *df, const double *C, int nocc, int prec, double *J, doub
   if (nocc != df->basis->nocc) return BQC_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const int n = df->basis->nbf;
+  // a NaN or an infinity in the orbitals would poison every element of J
+  // and K: refuse it on the host, before anything is copied or launched
+  for (size_t i = 0, e = (size_t)n * nocc; i < e; ++i)
+    if (!std::isfinite(C[i])) {
+      char msg[96];
+      std::snprintf(msg, sizeof(msg), "bqc_jk_host: C_occ[%zu] is not finite", i);
+      set_error(msg, __FILE__, __LINE__);
+      return BQC_E_INVALID;
+    }
   if (!df->host_io.p) {
     BQC_TRY(df->host_io.alloc(df->ctx, ((size_t)n * nocc + 2 * (size_t)n * n) * 8));
   }

@@ -588,7 +588,7 @@ static int launch3(const Eri3cArgs &a, int64_t total, cudaStream_t s) {
   BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int64_t blocks = (total + groups - 1) / groups;
-  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 16));
   kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
@@ -725,7 +725,7 @@ static int launch_schwarz_cls(const SchwarzArgs &a, cudaStream_t s) {
   BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int64_t blocks = (a.npair + groups - 1) / groups;
-  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 16));
   kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
@@ -810,7 +810,7 @@ static int launch_int2c_cls(const Int2cArgs &a, cudaStream_t s) {
                                     (int)smem));
   const int64_t total = (int64_t)a.nP * a.nQ;
   int64_t blocks = (total + groups - 1) / groups;
-  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 16));
   kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
@@ -930,7 +930,7 @@ static int launch_nuclear_cls(const OneArgs &a, cudaStream_t s) {
   BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int64_t blocks = (a.npair + groups - 1) / groups;
-  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 16));
   kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
   BQC_LAUNCH_CHECK();
   return BQC_OK;

@@ -38,7 +38,8 @@ static std::mutex g_mu;
 static void *g_scratch_dev[kMaxDevices] = {nullptr};
 
 // Device address of g_scratch on the current device (set up once per device,
-// with that device current).
+// with that device current, and kept for the life of the process; a
+// cudaDeviceReset() of the device leaves the kept address stale).
 static int scratch_address(void **out) {
   int dev = 0;
   BQC_CUDA_TRY(cudaGetDevice(&dev));

@@ -21,6 +21,28 @@ void set_error(const char *what, const char *file, int line) {
 }
 const char *last_error() { return g_err; }
 
+// Multiprocessor count of the current device, queried once per device.
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  if (dev >= 0 && dev < kMaxDev) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 1;  // no device: a one-SM plan is valid, only slower
+  }
+  if (dev >= 0 && dev < kMaxDev) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 void *Ctx::dmalloc(size_t bytes) {
   if (bytes == 0) bytes = 16;
   void *p = nullptr;

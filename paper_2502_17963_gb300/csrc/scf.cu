@@ -336,6 +336,8 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
                             mixed_iters >= std::max(2, o.max_iter / 2);
       if (emax < o.stage_tol || at_floor) {
         // switch to FP64: discard the mixed history, redo this iteration in FP64
+        res->switch_rule = emax < o.stage_tol ? BQC_SWITCH_STAGE_TOL : BQC_SWITCH_FLOOR;
+        res->switch_err = emax;
         stage = BQC_PREC_FP64;
         slot.clear();
         Bm.clear();

@@ -934,15 +934,8 @@ static MixedPlan mixed_plan(int n, int naux, int nocc, int nsm) {
   return m;
 }
 
-static int sm_count() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 152;
-}
-
 size_t mixed_workspace_bytes(int n, int naux, int nocc) {
-  const MixedPlan m = mixed_plan(n, naux, nocc, 152);
+  const MixedPlan m = mixed_plan(n, naux, nocc, sm_count());
   size_t b = (size_t)naux * n * m.ld * 4;            // Bl (Bh counted by the caller)
   b += (size_t)naux * n * (2 * m.ldx - nocc) * 4;    // Xh padding + Xl (Xh counted by caller)
   b += (size_t)2 * m.ldx * m.ld * 4 + (size_t)n * m.ldx * 4;
@@ -1293,13 +1286,13 @@ struct DirectMixed {
 void DirectMixedDeleter::operator()(DirectMixed *p) const { delete p; }
 
 size_t direct_mixed_bytes(int n, int naux, int nocc, int bs) {
-  const MixedPlan m = mixed_plan(n, naux, nocc, 152);
+  const MixedPlan m = mixed_plan(n, naux, nocc, sm_count());
   size_t b = (size_t)2 * n * bs * m.ld * 4;               // raw shadows of one sub-block
   const size_t nl = (size_t)round_up(naux, 4);
   b += (size_t)2 * n * m.ldx * nl * 4;                    // X^T / Y^T hi, lo
   b += (size_t)2 * naux * nl * 4;                         // L^{-1} hi, lo
   b += (size_t)3 * m.ldx * m.ld * 4;                      // C split + Cf
-  b += (size_t)m.ntri * std::max(1, 2 * 152 / std::max(1, m.ntri)) * kBM * kBM * 8;
+  b += (size_t)m.ntri * std::max(1, 2 * sm_count() / std::max(1, m.ntri)) * kBM * kBM * 8;
   return b;
 }
 
@@ -1498,3 +1491,31 @@ int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
 }
 
 }  // namespace bqc
+
+// ------------------------------------------- bounded-wait self-test -----
+
+namespace bqc {
+
+// One thread waits on an mbarrier that nothing ever arrives on, through the
+// same bounded wait the tensor-core kernels use; the wait gives up after
+// `limit` clocks and records code 99 in the context's device flag.
+__global__ void k_wait_selftest(int *flag, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, flag, 99, limit);
+}
+
+}  // namespace bqc
+
+extern "C" int bqc_wait_selftest(bqc_ctx *ctx, long long cycles, bqc_stream_t stream) {
+  if (!ctx || cycles <= 0 || cycles > 4000000000LL) return BQC_E_INVALID;
+  BQC_CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  bqc::k_wait_selftest<<<1, 32, 0, s>>>(ctx->flag, cycles);
+  BQC_LAUNCH_CHECK();
+  return ctx->check_flag(s);
+}

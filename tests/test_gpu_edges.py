@@ -128,3 +128,50 @@ def test_invalid_inputs(gpu_ctx, bqc):
     assert e.value.status == -1
     r = bqc.scf_run(gpu_ctx, df)
     assert r["converged"]
+
+
+def test_nonfinite_host_orbitals_rejected(gpu_ctx, bqc):
+    """Failure detection on the host: a NaN or an infinity in C_occ handed to
+    the end-to-end entry point is refused before any copy or launch, with the
+    offending index named, and the handle keeps working."""
+    w = workload.single_water()
+    basis = bqc.Basis(gpu_ctx, w)
+    df = bqc.DF(gpu_ctx, basis, keep_fp32=True)
+    rng = np.random.default_rng(3)
+    C = rng.standard_normal((basis.nbf, basis.nocc)) * 0.2
+    J0, K0 = df.jk_host(C, bqc.PREC_FP64)
+    for bad in (np.nan, np.inf, -np.inf):
+        Cb = C.copy()
+        Cb[7, 2] = bad
+        J = np.full((basis.nbf, basis.nbf), 123.0)
+        with pytest.raises(bqc.BqcError) as e:
+            df.jk_host(Cb, bqc.PREC_MIXED_TF32X3, J, J.copy())
+        assert e.value.status == -1
+        assert f"C_occ[{7 * basis.nocc + 2}]" in str(e.value)
+        assert (J == 123.0).all()  # nothing was written back
+    J1, K1 = df.jk_host(C, bqc.PREC_FP64)
+    assert np.array_equal(J0, J1) and np.array_equal(K0, K1)
+
+
+def test_bounded_device_wait_reports_flag(gpu_ctx, bqc):
+    """Failure detection on the device without a fault: a wait on a barrier
+    that nothing completes gives up after its clock limit (2e6 cycles, about
+    a millisecond), the kernel returns, the call reports BQC_E_DEVICE_FLAG,
+    and the context stays usable (a Fock build afterwards matches the oracle)."""
+    import torch
+    L = bqc.lib()
+    st = L.bqc_wait_selftest(gpu_ctx.h, 2_000_000, None)
+    assert st == -7, L.bqc_last_error()
+    assert b"code 99" in L.bqc_last_error()
+    assert L.bqc_wait_selftest(gpu_ctx.h, 0, None) == -1
+    w = workload.single_water()
+    basis = bqc.Basis(gpu_ctx, w)
+    df = bqc.DF(gpu_ctx, basis, keep_fp32=False)
+    rng = np.random.default_rng(11)
+    C = rng.standard_normal((basis.nbf, basis.nocc)) * 0.2
+    J, K = df.jk(torch.tensor(C, device="cuda"), bqc.PREC_FP64)
+    I = oracle.system_integrals(w)
+    B, _ = oracle.df_tensor(I["aux"], I["orb"])
+    Jr, Kr = oracle.jk_df(B, C)
+    assert np.abs(J.cpu().numpy() - Jr).max() < 1e-10
+    assert np.abs(K.cpu().numpy() - Kr).max() < 1e-10

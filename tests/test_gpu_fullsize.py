@@ -41,12 +41,34 @@ def setup(gpu_ctx):
     basis.close()
 
 
-def _oracle_K_block(mol, C, shells):
-    """Oracle K rows/cols for all functions of the given orbital shells."""
+def _schwarz_pair(mol, a, s):
+    """sqrt(max_ij (a_i s_j|a_i s_j)) from the oracle's 4-centre integrals of
+    the one- or two-shell basis {a, s}."""
+    sh = [mol.orb[a]] if a == s else [mol.orb[a], mol.orb[s]]
+    ob = oracle.OracleBasis(sh, mol.xyz)
+    eri = oracle.int4c(ob)
+    na = ob.ncart[0]
+    i0, j0 = (0, 0) if a == s else (0, na)
+    ni, nj = na, ob.ncart[-1]
+    d = [eri[i0 + i, j0 + j, i0 + i, j0 + j] for i in range(ni) for j in range(nj)]
+    return float(np.sqrt(max(abs(v) for v in d)))
+
+
+def _oracle_K_block(mol, C, shells, tau=None):
+    """Oracle K rows/cols for all functions of the given orbital shells.
+
+    With tau, the integrals (P|a s) of every aux shell P and orbital shell
+    pair whose Schwarz bound sqrt(max_p (p|p)) * sqrt(max_ij (a_i s_j|a_i s_j))
+    is below tau are set to zero before the fit (Sec. 2.2's prescreening, with
+    the bound the library documents), so that the oracle evaluates the same
+    screened method; the factors come from the oracle's own integrals."""
     aux = oracle.OracleBasis(mol.aux, mol.xyz)
     orb = oracle.OracleBasis(mol.orb, mol.xyz)
     V = oracle.int2c(aux)
     L = np.linalg.cholesky(V)
+    if tau is not None:
+        dV = np.diag(V)
+        qaux = np.array([np.sqrt(dV[aux.off[P]:aux.off[P + 1]].max()) for P in range(aux.nshell)])
     X, fns = [], []
     for a in shells:
         pairs = [(a, s) for s in range(orb.nshell)]
@@ -57,6 +79,10 @@ def _oracle_K_block(mol, C, shells):
         for s in range(orb.nshell):
             nb = orb.ncart[s]
             R[:, :, orb.off[s]:orb.off[s] + nb] = blk[:, col:col + na * nb].reshape(aux.nfn, na, nb)
+            if tau is not None:
+                q = _schwarz_pair(mol, a, s)
+                for P in np.nonzero(qaux * q < tau)[0]:
+                    R[aux.off[P]:aux.off[P + 1], :, orb.off[s]:orb.off[s] + nb] = 0.0
             col += na * nb
         B = sla.solve_triangular(L, R.reshape(aux.nfn, -1), lower=True).reshape(R.shape)
         X.append(np.einsum("pil,lk->pik", B, C, optimize=True))

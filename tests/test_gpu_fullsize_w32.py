@@ -1,0 +1,81 @@
+"""Full-matrix parity at (H2O)_32 (N = 800, Naux = 2400, nocc = 160) in the
+launch configuration bench.py times (stored DF with the split TF32 shadows,
+bqc_jk on the default stream).  At N >= 800 the FP64 J pass takes its
+single-chunk vectorised branch, as at (H2O)_64, so this size covers the code
+the benchmark runs.  The oracle forms B = L^-1 (Q|mu nu) with its own
+integrals and Cholesky factor, packed and solved in pair-column blocks, and
+J = sum_P w_P B_P, K = sum_P X_P X_P^T with X_P = B_P C summed over aux
+blocks (section 2.2 of the paper; the textbook DF J and K): every element of
+J and K is compared.  C_occ is a seeded orthonormal input.
+
+Bounds.  FP64: 1e-10 absolute (the FP64 J/K bar of the smaller tests), and
+the rounding scale of the contractions (JA = sum_P |w_P||B_P|,
+KA = sum_P |X_P|(|B_P||C|)^T + transpose) times 1e-11.  3xTF32: K within
+2^-14 KA (the bound of the other mixed tests); J reads the FP64 B, so its
+error is the fused w's, bounded by 2^-18 sum_P |B_P| wa_P with
+wa_P = sum_mu,i (|B_P||C|)_mu i |C|_mu i (three TF32 products per term, FP32
+accumulation in short chains).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def w32(gpu_ctx):
+    import torch
+    import paper_2502_17963_gb300 as bqc
+    mol = workload.water_cluster(32)
+    basis = bqc.Basis(gpu_ctx, mol)
+    assert (basis.nbf, basis.naux, basis.nocc) == (800, 2400, 160)
+    df = bqc.DF(gpu_ctx, basis, mode=bqc.DF_STORED, keep_fp32=True)
+    n = basis.nbf
+    rng = np.random.default_rng(3201)
+    C = np.linalg.qr(rng.standard_normal((n, basis.nocc)))[0] * 0.5
+    aux = oracle.OracleBasis(mol.aux, mol.xyz)
+    orb = oracle.OracleBasis(mol.orb, mol.xyz)
+    Bp, _ = oracle.df_tensor_packed(aux, orb)
+    Jo, Ko, JA, KA = oracle.jk_df_packed(Bp, n, C, block=48, bounds=True)
+    # the w-error scale of the mixed J: sum_P |B_P| wa_P
+    JW = np.zeros((n, n))
+    Ca = np.abs(C)
+    for P0 in range(0, Bp.shape[0], 48):
+        Ba = np.abs(oracle.unpack_rows(Bp[P0:P0 + 48], n))
+        wa = np.einsum("pmi,mi->p", np.einsum("pmn,ni->pmi", Ba, Ca, optimize=True), Ca)
+        JW += np.einsum("p,pmn->mn", wa, Ba, optimize=True)
+    del Bp
+    out = dict(bqc=bqc, df=df, basis=basis, Cg=torch.tensor(C, device="cuda"), Jo=Jo, Ko=Ko,
+               JA=JA, KA=KA, JW=JW)
+    yield out
+    df.close()
+    basis.close()
+    torch.cuda.empty_cache()
+
+
+def test_full_jk_w32_fp64(w32):
+    bqc, df = w32["bqc"], w32["df"]
+    J, K = df.jk(w32["Cg"], bqc.PREC_FP64)
+    J, K = J.cpu().numpy(), K.cpu().numpy()
+    dJ, dK = np.abs(J - w32["Jo"]), np.abs(K - w32["Ko"])
+    print(f"w32 FP64: max|dJ| {dJ.max():.3e} (ratio {(dJ / w32['JA']).max():.3e}), "
+          f"max|dK| {dK.max():.3e} (ratio {(dK / w32['KA']).max():.3e}), "
+          f"max|J| {np.abs(w32['Jo']).max():.3e}, max|K| {np.abs(w32['Ko']).max():.3e}")
+    assert dJ.max() < 1e-10 and dK.max() < 1e-10
+    assert (dJ <= 1e-11 * w32["JA"]).all() and (dK <= 1e-11 * w32["KA"]).all()
+
+
+def test_full_jk_w32_mixed_tf32x3(w32):
+    bqc, df = w32["bqc"], w32["df"]
+    J, K = df.jk(w32["Cg"], bqc.PREC_MIXED_TF32X3)
+    assert (J - J.T).abs().max().item() == 0.0 and (K - K.T).abs().max().item() == 0.0
+    J, K = J.cpu().numpy(), K.cpu().numpy()
+    dJ, dK = np.abs(J - w32["Jo"]), np.abs(K - w32["Ko"])
+    rK, rJ = (dK / w32["KA"]).max(), (dJ / w32["JW"]).max()
+    print(f"w32 3xTF32: max|dK| {dK.max():.3e} (ratio to KA {rK:.3e}), max|dJ| {dJ.max():.3e} "
+          f"(ratio to JW {rJ:.3e})")
+    assert rK < 2.0 ** -14
+    assert rJ < 2.0 ** -18

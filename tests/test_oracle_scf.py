@@ -139,3 +139,28 @@ def test_dimer_energy_invariance_with_d_and_f_shells():
     _, r1 = _scf(_rotate(m, R, np.array([-1.0, 0.5, 3.0])))
     assert r0.converged and r1.converged
     assert abs(r0.energy - r1.energy) < 1e-9
+
+
+def test_packed_aux_blocked_path_equals_plain_path():
+    """The aux-blocked oracle (packed B solved in column blocks, J/K summed
+    over P blocks) used at cluster sizes whose full-square B does not fit the
+    host: the same B, J and K as the plain definitions, on (H2O)_2 with odd
+    block sizes so that every block boundary is ragged; and its absolute
+    contractions bound the element magnitudes."""
+    mol = water_cluster(2)
+    I = oracle.system_integrals(mol)
+    B, L = oracle.df_tensor(I["aux"], I["orb"])
+    Bp, L2 = oracle.df_tensor_packed(I["aux"], I["orb"], col_block=97)
+    N = I["orb"].nfn
+    assert np.array_equal(L, L2)
+    assert np.abs(oracle.unpack_rows(Bp, N) - B).max() < 1e-14
+    rng = np.random.default_rng(5)
+    C = rng.standard_normal((N, mol.nocc)) * 0.3
+    J, K = oracle.jk_df(B, C)
+    J2, K2, JA, KA = oracle.jk_df_packed(Bp, N, C, block=13, bounds=True)
+    assert np.abs(J - J2).max() < 1e-12 * np.abs(J).max()
+    assert np.abs(K - K2).max() < 1e-12 * np.abs(K).max()
+    assert (np.abs(J) <= JA * (1 + 1e-12)).all() and (np.abs(K) <= KA * (1 + 1e-12)).all()
+    # the packed column of (mu, nu) is mu(mu+1)/2 + nu: spot-check one entry
+    mu, nu = 37, 11
+    assert Bp[5, mu * (mu + 1) // 2 + nu] == B[5, mu, nu] == B[5, nu, mu]
