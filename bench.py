@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--waters", type=int, default=64)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--prec", choices=["f16x3", "tf32x3"], default="f16x3",
+                    help="precision of the timed mixed build (split FP16 or split TF32)")
     ap.add_argument("--no-scf-check", action="store_true",
                     help="skip the staged-vs-plain-FP64 SCF energy check at the workload size")
     ap.add_argument("--no-baseline", action="store_true")
@@ -57,7 +59,9 @@ def parse():
     ap.add_argument("--serve-policy", choices=["backfill", "fifo"], default="backfill")
     ap.add_argument("--serve-precs", default="mixed_tf32x3,fp64")
     ap.add_argument("--scf", action="store_true",
-                    help="time one precision-staged SCF (3xTF32 then FP64) at --waters")
+                    help="time one precision-staged SCF (--prec, then FP64) at --waters")
+    ap.add_argument("--incremental", action="store_true",
+                    help="--scf: anchored incremental FP64 stage")
     ap.add_argument("--direct", action="store_true",
                     help="direct (on-the-fly) DF run, default (H2O)_128")
     return ap.parse_args()
@@ -230,10 +234,11 @@ def run_reference(args, rank, world):
 def config(mol, prec):
     n = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.orb)
     naux = sum((s.l + 1) * (s.l + 2) // 2 for s in mol.aux)
+    esz = 2 if "f16" in prec else 4
     return {"workload": f"{mol.name} DF-RHF Fock build, stored B, N={n}, Naux={naux}, "
                         f"nocc={mol.nocc}", "prec": prec, "seed": len(mol.Z) // 3,
-            "l2": f"inputs larger than L2 (per step: {naux * n * ((n + 3) // 4 * 4) * 8 / 1e9:.1f} GB "
-                  f"of split TF32 B shadows read by the X pass, {naux * n * (n + 1) / 2 * 8 / 1e9:.1f} GB "
+            "l2": f"inputs larger than L2 (per step: {naux * n * n * 2 * esz / 1e9:.1f} GB "
+                  f"of split B shadows read by the X pass, {naux * n * (n + 1) / 2 * 8 / 1e9:.1f} GB "
                   "of FP64 B by the J pass)",
             "parallelism": "replicas"}
 
@@ -252,7 +257,8 @@ def run_serve(args):
     ctx = bqc.Context(0)
     stream = workload.serving_stream(nreq=args.serve_requests, rate_hz=args.serve_rate)
     out = {}
-    precs = {"mixed_tf32x3": bqc.PREC_MIXED_TF32X3, "fp64": bqc.PREC_FP64}
+    precs = {"mixed_tf32x3": bqc.PREC_MIXED_TF32X3, "mixed_f16x3": bqc.PREC_MIXED_F16X3,
+             "fp64": bqc.PREC_FP64}
     for label in args.serve_precs.split(","):
         prec = precs[label]
         policy = {"backfill": bqc.SERVE_BACKFILL, "fifo": bqc.SERVE_FIFO}[args.serve_policy]
@@ -321,21 +327,26 @@ def run_scf(args):
     mol = workload.water_cluster(args.waters)
     ctx = bqc.Context(0)
     basis = bqc.Basis(ctx, mol)
+    f16 = args.prec == "f16x3"
+    prec = bqc.PREC_MIXED_F16X3 if f16 else bqc.PREC_MIXED_TF32X3
     t0 = time.perf_counter()
-    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED, keep_fp32=True)
+    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED,
+                keep_fp32=bqc.SHADOW_F16 if f16 else bqc.SHADOW_TF32)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     clocks = ClockSampler(gpu_index(0))
     clocks.start()
     t0 = time.perf_counter()
-    r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32X3)
+    r = bqc.scf_run(ctx, df, prec=prec, incremental=args.incremental)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     h = r["history"]
     nmix = sum(1 for p, _, _ in h if p != bqc.PREC_FP64)
     line = {"metric": "s per precision-staged DF-RHF SCF", "value": wall, "unit": "s",
-            "n_gpus": 1, "higher_is_better": False, "dtype": "tf32x3 then f64", "data": "synthetic",
+            "n_gpus": 1, "higher_is_better": False, "dtype": f"{args.prec} then f64",
+            "data": "synthetic", "fp64_stage": "incremental" if args.incremental else "full",
+            "builds": r["builds"],
             "config": {"workload": f"{mol.name} staged SCF from the core guess, N={basis.nbf}, "
                                    f"Naux={basis.naux}, nocc={basis.nocc}",
                        "stage_tol": 1e-5, "diis_tol": 1e-8},
@@ -398,26 +409,26 @@ def run_direct(args):
     print(json.dumps(line), flush=True)
 
 
-def staged_scf_check(bqc, ctx, df, torch):
-    """Staged SCF (3xTF32 first stage, then FP64) and plain FP64 SCF from the
-    core guess on one DF handle: wall times, Fock builds per stage, the stage
-    switch rule, and |E_staged - E_FP64|."""
+def staged_scf_check(bqc, ctx, df, torch, prec):
+    """Staged SCF (mixed first stage, then the anchored incremental FP64
+    stage, converged on a full FP64 build) and plain FP64 SCF from the core
+    guess on one DF handle: wall times, Fock builds by kind, the stage switch
+    rule, and |E_staged - E_FP64|."""
     no = df.basis.nocc
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rs = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32X3, keep_arrays=True)
+    rs = bqc.scf_run(ctx, df, prec=prec, keep_arrays=True, incremental=True)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     t0 = time.perf_counter()
     r64 = bqc.scf_run(ctx, df, prec=bqc.PREC_FP64)
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t0
-    h = rs["history"]
-    nmix = sum(1 for p, _, _ in h if p != bqc.PREC_FP64)
     dE = abs(rs["energy"] - r64["energy"])
     return {"E_staged_Eh": rs["energy"], "E_fp64_scf_Eh": r64["energy"], "abs_dE_Eh": dE,
             "meets_1e-6_Eh": bool(dE <= 1e-6 and rs["converged"] and r64["converged"]),
-            "staged": {"wall_s": ts, "fock_builds_mixed": nmix, "fock_builds_fp64": len(h) - nmix,
+            "staged": {"wall_s": ts, "fock_builds": rs["builds"], "first_stage_prec": prec,
+                       "fp64_stage": "anchored incremental (final build full FP64)",
                        "converged": rs["converged"], "diis_err": rs["diis_err"],
                        "switch_rule": rs["switch_rule"], "switch_err": rs["switch_err"],
                        "stage_tol": 1e-5},
@@ -459,8 +470,10 @@ def main():
     ctx = bqc.Context(local)
     basis = bqc.Basis(ctx, mol)
     n, no = basis.nbf, basis.nocc
+    MIX = bqc.PREC_MIXED_F16X3 if args.prec == "f16x3" else bqc.PREC_MIXED_TF32X3
     t0 = time.perf_counter()
-    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED, keep_fp32=True)
+    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED,
+                keep_fp32=bqc.SHADOW_F16 if args.prec == "f16x3" else bqc.SHADOW_TF32)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     scf = None
@@ -469,16 +482,15 @@ def main():
         # SCF (mixed, then FP64) against a plain FP64 SCF on the same DF
         # handle, both from the core guess; the timed builds below then run
         # at the converged occupied orbitals
-        scf = staged_scf_check(bqc, ctx, df, torch)
+        scf = staged_scf_check(bqc, ctx, df, torch, MIX)
         C = scf.pop("_C")
     else:
         # occupied orbitals of a physical state: two mixed SCF iterations from the core guess
-        r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_TF32X3, max_iter=2, keep_arrays=True)
+        r = bqc.scf_run(ctx, df, prec=MIX, max_iter=2, keep_arrays=True)
         C = r["C"][:, :no].contiguous()
     J = torch.empty((n, n), dtype=torch.float64, device="cuda")
     K = torch.empty_like(J)
     stream = torch.cuda.current_stream()
-    MIX = bqc.PREC_MIXED_TF32X3
     for _ in range(max(3, args.warmup)):
         df.jk(C, MIX, J, K)
     torch.cuda.synchronize()
@@ -508,9 +520,9 @@ def main():
     ph = np.array(phases)
     ph_mean = ph.mean(axis=0).tolist()
 
-    # single-pass TF32 (one product per term) for comparison
     tf1 = None
-    if True:
+    if args.prec == "tf32x3":
+        # single-pass TF32 (one product per term) for comparison
         df.jk(C, bqc.PREC_MIXED_TF32, J, K)
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
@@ -538,10 +550,11 @@ def main():
         per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.fp64_steps)]
         fms = statistics.median(per_step)
         D = C @ C.T  # E = sum D (H + F) + E_nn, so a build's energy error is sum D dF
-        df.jk(C, bqc.PREC_MIXED_TF32, J, K)
-        dF1 = 2.0 * (J - J64) - (K - K64)
-        tf1["max_abs_dF_vs_fp64"] = dF1.abs().max().item()
-        tf1["dE_vs_fp64_Eh"] = (D * dF1).sum().item()
+        if tf1 is not None:
+            df.jk(C, bqc.PREC_MIXED_TF32, J, K)
+            dF1 = 2.0 * (J - J64) - (K - K64)
+            tf1["max_abs_dF_vs_fp64"] = dF1.abs().max().item()
+            tf1["dE_vs_fp64_Eh"] = (D * dF1).sum().item()
         df.jk(C, MIX, J, K)
         dFm = 2.0 * (J - J64) - (K - K64)
         dF = dFm.abs().max().item()
@@ -580,21 +593,36 @@ def main():
     pk, pk_src = peaks()
     naux = basis.naux
     xalg = 2.0 * naux * n * n * no          # algorithmic flops of one X pass (2 Naux N^2 nocc)
-    xissued = 3 * xalg                      # 3xTF32 issues three products per term
+    xissued = 3 * xalg                      # the split issues three products per term
     xs = ph_mean[0] * 1e-3
-    xbytes = naux * n * n * 8 + naux * n * no * 8  # split B read + split X write
-    tf32_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")) * TF32_OVER_BF16
+    sust = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    if args.prec == "f16x3":
+        esz = 2
+        peak = sust  # dense fp16 and bf16 run at the same tensor rate
+        kern = "k_xpass<f16,XN,3,0> (X = B C, split FP16, 3 products)"
+        peak_src = f"{pk_src}: bf16 sustained (the fp16 dense rate equals bf16's)"
+        traffic = None  # no ncu capture of this kernel's DRAM bytes yet
+        traffic_src = "not captured for the FP16 kernel"
+    else:
+        esz = 4
+        peak = sust * TF32_OVER_BF16
+        kern = "k_xpass<tf32,XN,3,0> (X = B C, split TF32, 3 products)"
+        peak_src = f"{pk_src}: bf16 sustained x nominal tf32/bf16 (1.1/2.25)"
+        xb = naux * n * n * 8 + naux * n * no * 8
+        traffic = XPASS_TRAFFIC_RATIO * xb
+        traffic_src = ("ncu dram__bytes_read+write / algorithmic bytes of the same kernel at "
+                       f"(H2O)_16 ({XPASS_TRAFFIC_RATIO}) x this launch's bytes ({xb:.4g} B)")
+    xbytes = naux * n * n * 2 * esz + naux * n * no * 2 * esz  # hi+lo B shadows read, hi+lo X written
     achieved = xalg / xs / 1e12
-    roofline = {"bound": "tensor", "kernel": "k_xpass_tf32<XN,3,0> (X = B C, 3xTF32)",
-                "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "frac_issued": xissued / xs / 1e12 / tf32_peak,
-                "traffic": XPASS_TRAFFIC_RATIO * xbytes,
-                "traffic_source": "ncu dram__bytes_read+write / algorithmic bytes of the same kernel "
-                                  f"at (H2O)_16 ({XPASS_TRAFFIC_RATIO}) x this launch's "
-                                  f"bytes ({xbytes:.4g} B: hi+lo TF32 B shadows, hi+lo X)",
-                "peak_source": f"{pk_src}: bf16 sustained x nominal tf32/bf16 (1.1/2.25)",
+    roofline = {"bound": "tensor", "kernel": kern,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "frac_issued": xissued / xs / 1e12 / peak,
+                "traffic": traffic, "traffic_source": traffic_src,
+                "bytes_per_launch": xbytes,
+                "peak_source": peak_src,
                 "algorithmic_per_launch": f"2*Naux*N^2*nocc = {xalg:.4g} flop (frac); "
                                           f"3 products issued = {xissued:.4g} flop (frac_issued)"}
+    tf32_peak = peak
     jbytes = naux * n * (n + 1) / 2 * 8  # J pass: one read of the packed FP64 B
     kflops = n * n * naux * no           # SYRK half (algorithmic; 3 products issued)
     extra = {
@@ -606,6 +634,7 @@ def main():
                   "rate includes the contention (alone: 10.5 ms, 4.7 TB/s, FP64-pipe bound)",
         "k_syrk_tflops": kflops / (ph_mean[2] * 1e-3) / 1e12,
         "k_syrk_frac": kflops / (ph_mean[2] * 1e-3) / 1e12 / tf32_peak,
+        "tensor_peak_tflops": tf32_peak,
         "k_syrk_frac_issued": 3 * kflops / (ph_mean[2] * 1e-3) / 1e12 / tf32_peak,
         "staged_scf": scf,
         "setup_s": setup_s,
@@ -614,8 +643,8 @@ def main():
     }
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
-            "config": config(mol, "mixed_tf32x3"), "roofline": roofline,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": config(mol, "mixed_" + args.prec), "roofline": roofline,
             "gpu_launches": 7 * args.steps, "clocks": clk, "e2e": e2e}
     line.update(extra)
     if not args.no_baseline and world >= 1:

@@ -64,11 +64,16 @@ enum {
  * hi + lo into two TF32 parts and three products per term (hi*hi + hi*lo +
  * lo*hi, ~2^-22); J in FP64 from the FP64 B on the CUDA cores, concurrently
  * with the tensor-core passes (the direct mode's J is FP64 in every
- * precision). */
+ * precision).  MIXED_F16X3: as MIXED_TF32X3 with FP16 split parts (FP16 has
+ * TF32's 11-bit significand; B, C_occ and X are scaled by powers of two to a
+ * largest magnitude of 2^14 before the split, so the narrow FP16 exponent
+ * range costs nothing above ~2^-40 of the largest element) and kind::f16
+ * MMAs, which run at twice the TF32 rate; stored mode only. */
 typedef enum {
   BQC_PREC_FP64 = 0,
   BQC_PREC_MIXED_TF32 = 1,
-  BQC_PREC_MIXED_TF32X3 = 2
+  BQC_PREC_MIXED_TF32X3 = 2,
+  BQC_PREC_MIXED_F16X3 = 3
 } bqc_prec;
 
 typedef struct bqc_ctx bqc_ctx;
@@ -138,12 +143,18 @@ int bqc_int3c(const bqc_basis *basis, double schwarz, double *out_dev, bqc_strea
 
 typedef enum { BQC_DF_STORED = 0, BQC_DF_DIRECT = 1, BQC_DF_AUTO = 2 } bqc_df_mode;
 
+/* Split shadows of B kept for the mixed precisions: NONE (FP64 builds only),
+ * TF32 (full-square hi/lo TF32 parts: MIXED_TF32 and MIXED_TF32X3; 8 bytes
+ * per element of the square), F16 (scaled hi/lo FP16 parts: MIXED_F16X3;
+ * 4 bytes per element).  Direct mode uses TF32 for either non-NONE value. */
+enum { BQC_SHADOW_NONE = 0, BQC_SHADOW_TF32 = 1, BQC_SHADOW_F16 = 2 };
+
 typedef struct {
   int mode;            /* bqc_df_mode                                         */
   double schwarz;      /* screening threshold; default 1e-12 stored, 1e-10 direct */
   int aux_block;       /* direct mode: aux functions per block (default 1024)  */
-  int keep_fp32;       /* stored mode: also keep the split TF32 full-square shadows
-                          (needed by the mixed precisions)                     */
+  int keep_fp32;       /* split shadows of B for the mixed precisions: one of
+                          BQC_SHADOW_NONE / _TF32 / _F16 (default TF32)       */
   size_t hbm_limit;    /* AUTO: choose DIRECT when STORED needs more (0 = free memory) */
 } bqc_df_opts;
 
@@ -222,6 +233,24 @@ int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, 
 int bqc_df_timing(bqc_df *df, int enable);
 int bqc_df_phase_ms(bqc_df *df, float *ms, int n);
 
+/* --------------------------------------------------------------- MP2 --- */
+
+/* Closed-shell DF-MP2 correlation energy on the resident three-index tensor
+ * (Sec. 2.3: MO-basis tensor B_P,ia = sum C_mu,i B_P,mu nu C_nu,a, integrals
+ * (ia|jb) = sum_P B_P,ia B_P,jb formed block by block, the denominator
+ * applied in place):
+ *   E2 = sum_{i,j,a,b} (ia|jb) [2 (ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b).
+ * df: a stored-mode handle.  C_dev: N x nmo row-major canonical orbitals
+ * (columns; the first nocc occupied, the rest virtual), eps_dev: their nmo
+ * orbital energies (bqc_scf_run's C_dev / eps_dev outputs have this layout).
+ * prec: BQC_PREC_FP64 (DFMA GEMMs); other precisions BQC_E_UNSUPPORTED.
+ * Writes *e2 (host).  Allocates its working memory from the context
+ * (Naux * nocc * nvir doubles and a block of (ia|jb) of at most 1 GiB) and
+ * synchronises the stream; reuses the handle's X buffer, so it must not
+ * overlap a bqc_jk on the same handle. */
+int bqc_mp2(bqc_df *df, const double *C_dev, const double *eps_dev, int nmo, int prec,
+            double *e2, bqc_stream_t stream);
+
 /* ---------------------------------------------------------------- SCF --- */
 
 typedef struct {
@@ -234,6 +263,9 @@ typedef struct {
   int diis_space;      /* default 8                                           */
   int prec;            /* bqc_prec of the first stage; FP64 = unstaged        */
   double orth_thresh;  /* canonical orthogonalisation cut on S eigenvalues (1e-8) */
+  int incremental;     /* staged SCF only (prec mixed): 0 = every FP64-stage Fock
+                          build is a full FP64 build; 1 = anchored incremental
+                          FP64 stage (see bqc_scf_run)                         */
 } bqc_scf_opts;
 
 typedef struct {
@@ -264,13 +296,32 @@ typedef struct {
    * mixed iteration. */
   int switch_rule;
   double switch_err;
+  /* Fock builds of the run by kind (output): full FP64 builds, mixed builds of
+   * the first stage, incremental FP64-stage builds (opts.incremental). */
+  int builds_fp64;
+  int builds_mixed;
+  int builds_incremental;
 } bqc_scf_result;
 
 enum { BQC_SWITCH_NONE = 0, BQC_SWITCH_STAGE_TOL = 1, BQC_SWITCH_FLOOR = 2 };
 
 /* Closed-shell SCF (canonical orthogonalisation, core-Hamiltonian guess,
  * Pulay DIIS on e = X^T (FDS - SDF) X, aufbau) with the Fock build of
- * bqc_jk.  With prec = MIXED_TF32 the first stage runs mixed and switches to
+ * bqc_jk.
+ * Anchored incremental FP64 stage (opts.incremental = 1 with a mixed first
+ * stage; no counterpart in the paper, the incremental Fock build of direct
+ * SCF codes): F_k = F_(k-1) + 2 J[dD] - K[dD] with dD = D_k - D_(k-1)
+ * factored as V+ V+^T - V- V-^T (eigenvectors of dD scaled by the square
+ * roots of its positive and negative eigenvalues, at most nocc of each) and
+ * J, K of V+ and V- built in the first stage's mixed precision, so the
+ * rounding error of an increment scales with |dD|, not with |D|.  Full FP64
+ * builds ("anchors") reset the accumulated error: at the switch, when the
+ * DIIS error first falls below 100 x diis_tol, after 10 increments, and on
+ * every iteration that would converge, so convergence (max|e| < diis_tol and
+ * |dE| below the energy bar) is only ever declared on a full FP64 Fock
+ * matrix and the reported energy is that build's.  After 8 anchors the
+ * stage falls back to full builds.  History entries of incremental builds
+ * carry the precision code -1.  With prec = MIXED_TF32 the first stage runs mixed and switches to
  * FP64 (DIIS subspace cleared) when the DIIS error drops below stage_tol, or
  * earlier once the mixed stage stops improving (its error floor, about
  * max|dF_mixed| / sqrt(smallest kept overlap eigenvalue), can lie above
@@ -340,8 +391,9 @@ int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res);
  * requests are done; BQC_E_TIMEOUT otherwise. */
 int bqc_serve_drain(bqc_server *srv, double timeout_s);
 int bqc_serve_destroy(bqc_server *srv);
-/* Predicted device bytes of a request of this size (the admission ledger). */
-size_t bqc_serve_footprint(int nbf, int naux, int nocc);
+/* Predicted device bytes of a request of this size solved with `prec` (the
+ * admission ledger); 0 for an invalid argument. */
+size_t bqc_serve_footprint(int nbf, int naux, int nocc, int prec);
 
 /* Failure-detection self-test (no counterpart in the paper): launches one
  * kernel whose only thread waits on a device barrier that nothing completes,

@@ -25,6 +25,8 @@ BQC_E_NOT_READY = -8
 PREC_FP64 = 0
 PREC_MIXED_TF32 = 1
 PREC_MIXED_TF32X3 = 2
+PREC_MIXED_F16X3 = 3
+SHADOW_NONE, SHADOW_TF32, SHADOW_F16 = 0, 1, 2
 SERVE_BACKFILL, SERVE_FIFO = 0, 1
 DF_STORED, DF_DIRECT, DF_AUTO = 0, 1, 2
 
@@ -53,7 +55,7 @@ class bqc_scf_opts(ctypes.Structure):
     _fields_ = [("diis_tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
                 ("stage_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_space", ctypes.c_int), ("prec", ctypes.c_int),
-                ("orth_thresh", ctypes.c_double)]
+                ("orth_thresh", ctypes.c_double), ("incremental", ctypes.c_int)]
 
 
 class bqc_scf_result(ctypes.Structure):
@@ -63,7 +65,9 @@ class bqc_scf_result(ctypes.Structure):
                 ("nmo", ctypes.c_int), ("C_dev", ctypes.c_void_p), ("eps_dev", ctypes.c_void_p),
                 ("F_dev", ctypes.c_void_p), ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int),
-                ("switch_rule", ctypes.c_int), ("switch_err", ctypes.c_double)]
+                ("switch_rule", ctypes.c_int), ("switch_err", ctypes.c_double),
+                ("builds_fp64", ctypes.c_int), ("builds_mixed", ctypes.c_int),
+                ("builds_incremental", ctypes.c_int)]
 
 
 class bqc_serve_opts(ctypes.Structure):
@@ -127,8 +131,9 @@ _SIGS = {
     "bqc_serve_poll": (ip, [vp, ctypes.c_uint64, ctypes.POINTER(bqc_serve_result)]),
     "bqc_serve_drain": (ip, [vp, dp]),
     "bqc_serve_destroy": (ip, [vp]),
-    "bqc_serve_footprint": (ctypes.c_size_t, [ip, ip, ip]),
+    "bqc_serve_footprint": (ctypes.c_size_t, [ip, ip, ip, ip]),
     "bqc_wait_selftest": (ip, [vp, ctypes.c_longlong, vp]),
+    "bqc_mp2": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
 }
 
 
@@ -313,9 +318,13 @@ class DF:
     """bqc_df: the density-fitting tensor (stored) or its on-the-fly machinery (direct)."""
 
     def __init__(self, ctx: Context, basis: Basis, mode: int = DF_STORED, schwarz: float = -1.0,
-                 aux_block: int = 1024, keep_fp32: bool = True, hbm_limit: int = 0, stream=None):
+                 aux_block: int = 1024, keep_fp32=True, hbm_limit: int = 0, stream=None):
+        """keep_fp32: True / SHADOW_TF32 (split TF32 shadows), SHADOW_F16 (split
+        FP16 shadows, for PREC_MIXED_F16X3), False / SHADOW_NONE (FP64 only)."""
         self.ctx, self.basis = ctx, basis
-        o = bqc_df_opts(mode, schwarz, aux_block, 1 if keep_fp32 else 0, hbm_limit)
+        shadow = SHADOW_TF32 if keep_fp32 is True else (SHADOW_NONE if keep_fp32 is False
+                                                          else int(keep_fp32))
+        o = bqc_df_opts(mode, schwarz, aux_block, shadow, hbm_limit)
         h = vp()
         check(lib().bqc_df_build(ctx.h, basis.h, ctypes.byref(o), _stream_ptr(stream),
                                  ctypes.byref(h)), "bqc_df_build")
@@ -379,16 +388,29 @@ class DF:
             pass
 
 
+def mp2(df: DF, C, eps, prec: int = PREC_FP64, stream=None) -> float:
+    """DF-MP2 correlation energy from canonical orbitals C (N x nmo device
+    tensor, occupied first) and orbital energies eps (nmo device tensor)."""
+    e2 = ctypes.c_double()
+    C = C.contiguous()
+    eps = eps.contiguous()
+    check(lib().bqc_mp2(df.h, _ptr(C), _ptr(eps), C.shape[1], prec, ctypes.byref(e2),
+                        _stream_ptr(stream)), "bqc_mp2")
+    return e2.value
+
+
 def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
             energy_tol: float = 1e-10, stage_tol: float = 1e-5, max_iter: int = 100,
-            diis_space: int = 8, orth_thresh: float = 1e-8, stream=None, keep_arrays=False):
+            diis_space: int = 8, orth_thresh: float = 1e-8, stream=None, keep_arrays=False,
+            incremental: bool = False):
     """Runs bqc_scf_run; returns a dict (energy, iterations, converged, ...,
     history = [(prec, DIIS error, energy)] per Fock build).
 
     With keep_arrays the MO coefficients (N x nmo), orbital energies and the
     last Fock matrix come back as device tensors.
     """
-    o = bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space, prec, orth_thresh)
+    o = bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space, prec, orth_thresh,
+                     1 if incremental else 0)
     r = bqc_scf_result()
     n = df.basis.nbf
     cap = 2 * max_iter + 2
@@ -404,6 +426,8 @@ def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
                converged=bool(r.converged), iterations_mixed=r.iterations_mixed, nmo=r.nmo,
                switch_rule={0: None, 1: "stage_tol", 2: "floor"}.get(r.switch_rule),
                switch_err=r.switch_err if r.switch_rule else None,
+               builds={"fp64": r.builds_fp64, "mixed": r.builds_mixed,
+                       "incremental": r.builds_incremental},
                history=[(int(hist[3 * i]), hist[3 * i + 1], hist[3 * i + 2])
                         for i in range(r.history_len)])
     if keep_arrays:
@@ -417,11 +441,13 @@ class Server:
     def __init__(self, ctx: Context, max_slots: int = 4, hbm_budget: int = 0,
                  prec: int = PREC_MIXED_TF32X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
                  stage_tol: float = 1e-5, max_iter: int = 100, diis_space: int = 8,
-                 orth_thresh: float = 1e-8, policy: int = 0, max_skips: int = 8):
+                 orth_thresh: float = 1e-8, policy: int = 0, max_skips: int = 8,
+                 incremental: bool = False):
         self.ctx = ctx
         o = bqc_serve_opts(max_slots, hbm_budget, prec,
                            bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space,
-                                        prec, orth_thresh), policy, max_skips)
+                                        prec, orth_thresh, 1 if incremental else 0),
+                           policy, max_skips)
         h = vp()
         check(lib().bqc_serve_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "bqc_serve_create")
         self.h = h
@@ -460,5 +486,5 @@ class Server:
             pass
 
 
-def serve_footprint(nbf: int, naux: int, nocc: int) -> int:
-    return int(lib().bqc_serve_footprint(nbf, naux, nocc))
+def serve_footprint(nbf: int, naux: int, nocc: int, prec: int = PREC_MIXED_TF32X3) -> int:
+    return int(lib().bqc_serve_footprint(nbf, naux, nocc, prec))

@@ -180,17 +180,13 @@ int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s
   return BQC_OK;
 }
 
-size_t df_stored_bytes(int n, int naux, int nocc, bool fp32) {
+size_t df_stored_bytes(int n, int naux, int nocc, int shadow) {
   const size_t npair = (size_t)n * (n + 1) / 2;
   size_t b = (size_t)naux * naux * 8 + (size_t)naux * npair * 8;  // L, B64
   b += (size_t)naux * n * nocc * 8;                                // X64
   b += (size_t)jpass_split((int64_t)npair, naux) * npair * 8 + (size_t)naux * 8 * 2;
-  if (fp32) {
-    b += (size_t)naux * n * mixed_ld(n) * 4;  // B32 (hi part)
-    b += (size_t)naux * n * nocc * 4;       // X32
-    b += (size_t)n * nocc * 4 * 2;          // C shadows
-    b += mixed_workspace_bytes(n, naux, nocc);
-  }
+  if (shadow == BQC_SHADOW_TF32 || shadow == BQC_SHADOW_F16)
+    b += mixed_workspace_bytes(n, naux, nocc, shadow);
   return b;
 }
 
@@ -223,9 +219,10 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
       BQC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
       limit = (size_t)(fr * 0.9);
     }
-    mode = df_stored_bytes(n, naux, no, o.keep_fp32 != 0) <= limit ? BQC_DF_STORED : BQC_DF_DIRECT;
+    mode = df_stored_bytes(n, naux, no, o.keep_fp32) <= limit ? BQC_DF_STORED : BQC_DF_DIRECT;
   }
   if (mode != BQC_DF_STORED && mode != BQC_DF_DIRECT) return BQC_E_INVALID;
+  if (o.keep_fp32 < BQC_SHADOW_NONE || o.keep_fp32 > BQC_SHADOW_F16) return BQC_E_INVALID;
   if (o.schwarz < 0.0) o.schwarz = (mode == BQC_DF_STORED) ? 1e-12 : 1e-10;
   if (o.aux_block <= 0) o.aux_block = 1024;
   bqc_df *df = new (std::nothrow) bqc_df();
@@ -266,11 +263,8 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
     if ((st = df->X64.alloc(ctx, (size_t)naux * n * no * 8)) != BQC_OK) return fail(st);
     if ((st = df->Jp.alloc(ctx, (size_t)jpass_split(npair, naux) * npair * 8)) != BQC_OK)
       return fail(st);
-    if (o.keep_fp32) {
-      if ((st = df->B32.alloc(ctx, (size_t)naux * n * mixed_ld(n) * 4)) != BQC_OK)
-        return fail(st);
-      if ((st = mixed_setup(df, s)) != BQC_OK) return fail(st);
-    }
+    if (o.keep_fp32 != BQC_SHADOW_NONE)
+      if ((st = mixed_setup(df, o.keep_fp32, s)) != BQC_OK) return fail(st);
   } else {
     if ((st = direct_setup(df, s)) != BQC_OK) return fail(st);
   }
@@ -357,8 +351,12 @@ int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K
   df->last_mixed = prec != BQC_PREC_FP64;
   if (df->mode == BQC_DF_DIRECT) return jk_direct(df, C, prec, J, K, s);
   if (prec == BQC_PREC_FP64) return jk_fp64_stored(df, C, J, K, s);
-  if (prec == BQC_PREC_MIXED_TF32 || prec == BQC_PREC_MIXED_TF32X3) {
-    if (!df->B32.p) return BQC_E_INVALID;
+  if (prec == BQC_PREC_MIXED_TF32 || prec == BQC_PREC_MIXED_TF32X3 ||
+      prec == BQC_PREC_MIXED_F16X3) {
+    if (!df->mixed) {
+      set_error("mixed precision needs split shadows (bqc_df_opts.keep_fp32)", __FILE__, __LINE__);
+      return BQC_E_INVALID;
+    }
     return jk_mixed_stored(df, C, prec, J, K, s);
   }
   return BQC_E_INVALID;

@@ -7,6 +7,7 @@
 namespace bqc {
 
 struct MixedState;
+size_t mixed_bytes(const MixedState *ms);
 struct MixedDeleter {
   void operator()(MixedState *p) const;
 };
@@ -31,7 +32,7 @@ struct Df {
   DBuf w;      // Naux FP64: w_P = B_P : D
   DBuf host_io;
   // mixed precision (TF32 tensor cores)
-  DBuf B32;    // Naux x N x N, TF32-rounded FP32, full square (MMA A operand)
+  DBuf B32;    // Naux x N x ld, TF32 hi part of B, full square (MMA A operand)
   DBuf X32;    // Naux x N x nocc_pad FP32
   DBuf Ct32;   // nocc_pad x N FP32 (C_occ^T, TF32-rounded: MMA B operand, K-major)
   DBuf wpart;  // per X-pass tile partial w (FP64)
@@ -66,13 +67,16 @@ struct Df {
   size_t device_bytes() const {
     return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +
            wpart.n + Kpart.n + raw.n + Linv.n + Xraw.n + gamma.n + D2.n +
-           plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n;
+           plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n +
+           mixed_bytes(mixed.get());
   }
 };
 
-size_t mixed_workspace_bytes(int n, int naux, int nocc);
+// Device bytes of the mixed-precision state beyond the Df buffers (shadow:
+// BQC_SHADOW_TF32 or BQC_SHADOW_F16).
+size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow);
 int mixed_ld(int n);  // row length of the TF32 shadow (N rounded up to 4)
-int mixed_setup(Df *df, cudaStream_t s);
+int mixed_setup(Df *df, int shadow, cudaStream_t s);
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 // J = sum_P w_P B_P from the packed FP64 B and df->w (FP64), full symmetric.
@@ -84,7 +88,7 @@ int direct_mixed_prep_c(Df *df, const double *C, int split, cudaStream_t s);
 int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cudaStream_t s);
 int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s);
 int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
-size_t df_stored_bytes(int n, int naux, int nocc, bool fp32);
+size_t df_stored_bytes(int n, int naux, int nocc, int shadow);
 
 }  // namespace bqc
 

@@ -139,6 +139,10 @@ int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStrea
   const int n = b->nbf, naux = b->naux, no = b->nocc;
   const int64_t npair = df->npair;
   const int bk = df->aux_block;
+  if (prec == BQC_PREC_MIXED_F16X3) {
+    set_error("direct mode runs FP64, MIXED_TF32 and MIXED_TF32X3 builds", __FILE__, __LINE__);
+    return BQC_E_UNSUPPORTED;
+  }
   const bool mixed = prec != BQC_PREC_FP64;
   const int split = prec == BQC_PREC_MIXED_TF32X3 ? 3 : 1;
   if (mixed && !df->dmixed) return BQC_E_INVALID;

@@ -73,7 +73,37 @@ __global__ void k_cm_to_rm(int rows, int cols, const double *in, int64_t ld, dou
   out[i] = in[c * ld + r];
 }
 
+// V[nu][c] = U[k0 + c][nu] * sqrt(|ev[k0 + c]|) for c < cnt, 0 for cnt <= c < ncol
+// (U column-major n x n eigenvectors; V row-major n x ncol): the scaled
+// eigenvector factor of one sign of a symmetric matrix.
+__global__ void k_eig_factor(int n, const double *U, const double *ev, int k0, int cnt,
+                             int ncol, double *V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * ncol) return;
+  const int64_t nu = i / ncol;
+  const int c = (int)(i % ncol);
+  V[i] = c < cnt ? U[(int64_t)(k0 + c) * n + nu] * sqrt(fabs(ev[k0 + c])) : 0.0;
+}
+
+// F = Fref + 2 (Jp - Jm) - (Kp - Km)
+__global__ void k_inc_fock(int64_t n, const double *Fref, const double *Jp, const double *Jm,
+                           const double *Kp, const double *Km, double *F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) F[i] = Fref[i] + 2.0 * (Jp[i] - Jm[i]) - (Kp[i] - Km[i]);
+}
+
 static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// Instantiated CUDA graphs of the Fock build, one per precision, destroyed on
+// every exit path.
+struct GraphSet {
+  cudaGraphExec_t g[4] = {nullptr, nullptr, nullptr, nullptr};
+  void clear() {
+    for (auto &e : g)
+      if (e) cudaGraphExecDestroy(e), e = nullptr;
+  }
+  ~GraphSet() { clear(); }
+};
 
 // Solves the (m+1) x (m+1) Pulay system by Gaussian elimination with partial
 // pivoting; returns false if singular.
@@ -221,11 +251,65 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   double E = 0.0, Eprev = 0.0, emax = INFINITY;
   bool have_prev = false, converged = false;
   int it = 0;
+  // anchored incremental FP64 stage (see bqc.h): state
+  const bool inc_on = o.incremental != 0 && o.prec != BQC_PREC_FP64;
+  const int mixed_prec = o.prec;
+  DBuf Facc, Dref, Dk, Vp, Vm, J2, K2, evd;
+  if (inc_on) {
+    for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2}) BQC_TRY(p->alloc(ctx, nn * 8));
+    BQC_TRY(evd.alloc(ctx, (size_t)n * 8));
+    BQC_TRY(Vp.alloc(ctx, (size_t)n * no * 8));
+    BQC_TRY(Vm.alloc(ctx, (size_t)n * no * 8));
+  }
+  bool need_anchor = true;    // the first FP64-stage build is full
+  bool last_incremental = false;
+  int anchors = 0, inc_since_anchor = 0;
+  double anchor_err = INFINITY;
+  std::vector<double> hev;
   // The Fock build of an iteration (C -> C_occ row-major, J, K, F) has no
   // host synchronisation in stored mode, so it is captured once per precision
   // stage into a CUDA graph and replayed (thread-local capture mode: other
   // threads, e.g. other serving slots, keep launching meanwhile).
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  GraphSet graphs;
+  cudaGraphExec_t *gexec = graphs.g;
+  // F = Facc + G[D_k - Dref] in the mixed precision (no graph: the
+  // eigen-decomposition reads its status on the host).
+  auto incremental_build = [&]() -> int {
+    BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, no, &one, Cc.as<double>(), n,
+                             Cc.as<double>(), n, &zero, Dk.as<double>(), n));
+    const double mone = -1.0;
+    BQC_BLAS_TRY(cublasDgeam(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, &one, Dk.as<double>(), n,
+                             &mone, Dref.as<double>(), n, t1.as<double>(), n));
+    BQC_TRY(eigh(w, ctx, t1.as<double>(), n, evd.as<double>(), work, info, s));
+    hev.resize(n);
+    BQC_CUDA_TRY(cudaMemcpyAsync(hev.data(), evd.p, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    BQC_CUDA_TRY(cudaStreamSynchronize(s));
+    double amax = 0.0;
+    for (double v : hev) amax = std::max(amax, std::fabs(v));
+    const double thr = amax * 1e-15;
+    int nneg = 0, npos = 0;
+    while (nneg < n && hev[nneg] < -thr) ++nneg;
+    while (npos < n - nneg && hev[n - 1 - npos] > thr) ++npos;
+    nneg = std::min(nneg, no);  // most negative first
+    npos = std::min(npos, no);  // the largest positive ones are the last
+    const unsigned g = nblk((int64_t)n * no);
+    k_eig_factor<<<g, 256, 0, s>>>(n, t1.as<double>(), evd.as<double>(), 0, nneg, no,
+                                   Vm.as<double>());
+    BQC_LAUNCH_CHECK();
+    k_eig_factor<<<g, 256, 0, s>>>(n, t1.as<double>(), evd.as<double>(), n - npos, npos, no,
+                                   Vp.as<double>());
+    BQC_LAUNCH_CHECK();
+    BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Vp.as<double>(), no, mixed_prec, J.as<double>(),
+                   K.as<double>(), (bqc_stream_t)s));
+    BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Vm.as<double>(), no, mixed_prec, J2.as<double>(),
+                   K2.as<double>(), (bqc_stream_t)s));
+    k_inc_fock<<<nblk(nn), 256, 0, s>>>(nn, Facc.as<double>(), J.as<double>(), J2.as<double>(),
+                                        K.as<double>(), K2.as<double>(), F.as<double>());
+    BQC_LAUNCH_CHECK();
+    BQC_CUDA_TRY(cudaMemcpyAsync(Facc.p, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+    BQC_CUDA_TRY(cudaMemcpyAsync(Dref.p, Dk.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+    return BQC_OK;
+  };
   auto fock_build = [&](int prec) -> int {
     k_cm_to_rm<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, Cc.as<double>(), n, Crm.as<double>());
     BQC_LAUNCH_CHECK();
@@ -237,12 +321,15 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     return BQC_OK;
   };
   const bool use_graph = df->mode == BQC_DF_STORED && !df->timing && s != nullptr;
-  auto graph_free = [&]() {
-    for (auto &g : gexec)
-      if (g) cudaGraphExecDestroy(g), g = nullptr;
-  };
+  auto graph_free = [&]() { graphs.clear(); };
   for (it = 1; it <= o.max_iter; ++it) {
-    if (use_graph && stage >= 0 && stage < 3) {
+    const bool inc_stage = inc_on && stage == BQC_PREC_FP64 && anchors < 8;
+    last_incremental = inc_stage && !need_anchor;
+    if (last_incremental) {
+      BQC_TRY(incremental_build());
+      ++res->builds_incremental;
+      ++inc_since_anchor;
+    } else if (use_graph && stage >= 0 && stage < 4) {
       if (!gexec[stage]) {
         cudaGraph_t graph = nullptr;
         BQC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -269,8 +356,14 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     } else {
       BQC_TRY(fock_build(stage));
     }
+    if (!last_incremental) ++(stage == BQC_PREC_FP64 ? res->builds_fp64 : res->builds_mixed);
     BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, no, &one, Cc.as<double>(), n,
                              Cc.as<double>(), n, &zero, D.as<double>(), n));
+    if (inc_stage && !last_incremental) {
+      // an anchor: the reference of the next increments
+      BQC_CUDA_TRY(cudaMemcpyAsync(Facc.p, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+      BQC_CUDA_TRY(cudaMemcpyAsync(Dref.p, D.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+    }
     k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, F.as<double>(), 1.0, nullptr, 0.0,
                                       t2.as<double>());
     BQC_LAUNCH_CHECK();
@@ -307,14 +400,32 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     emax = std::fabs(hv);
     if (res->history && res->history_len < res->history_cap) {
       double *h = res->history + 3 * (size_t)res->history_len++;
-      h[0] = stage;
+      h[0] = last_incremental ? -1.0 : stage;
       h[1] = emax;
       h[2] = E;
     }
     if (stage == BQC_PREC_FP64 && emax < o.diis_tol && have_prev &&
         std::fabs(E - Eprev) < std::max(o.energy_tol, DBL_EPSILON * n * std::fabs(E))) {
-      converged = true;
-      break;
+      if (!last_incremental) {
+        converged = true;
+        break;
+      }
+      // converged on an incremental Fock matrix: redo the iteration as a
+      // full FP64 build and test again
+      need_anchor = true;
+      --it;
+      continue;
+    }
+    if (inc_stage) {
+      if (!last_incremental) {
+        ++anchors;
+        anchor_err = emax;
+        inc_since_anchor = 0;
+        need_anchor = false;
+      } else if ((emax < 100.0 * o.diis_tol && anchor_err >= 100.0 * o.diis_tol) ||
+                 inc_since_anchor >= 10) {
+        need_anchor = true;  // the next build is full
+      }
     }
     if (stage != BQC_PREC_FP64) {
       // Switch to FP64 at stage_tol, or once the mixed stage has reached its

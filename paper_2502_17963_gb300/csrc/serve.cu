@@ -164,11 +164,18 @@ struct bqc_server {
 
 namespace bqc {
 
+// Shadow kind a precision needs.
+static int shadow_of_prec(int prec) {
+  return prec == BQC_PREC_MIXED_F16X3 ? BQC_SHADOW_F16
+         : prec == BQC_PREC_FP64      ? BQC_SHADOW_NONE
+                                      : BQC_SHADOW_TF32;
+}
+
 // Predicted device bytes of one solve: stored DF tensors (FP64 B, split TF32
 // shadows, X), the integral screening plan, and the SCF work matrices.
-size_t serve_footprint(int n, int naux, int nocc, bool mixed) {
+size_t serve_footprint(int n, int naux, int nocc, int shadow) {
   const size_t nn = (size_t)n * n;
-  size_t b = df_stored_bytes(n, naux, nocc, mixed);
+  size_t b = df_stored_bytes(n, naux, nocc, shadow);
   b += (size_t)naux * naux * 8;             // metric copy during the build
   b += (size_t)(16 + 2 * 8) * nn * 8;       // SCF matrices + DIIS history
   b += (size_t)3 * n * n / 2 * 16;          // shell-pair plan (generous)
@@ -196,7 +203,7 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
     o.mode = BQC_DF_STORED;
     o.schwarz = -1.0;
     o.aux_block = 1024;
-    o.keep_fp32 = srv->opts.prec != BQC_PREC_FP64;
+    o.keep_fp32 = shadow_of_prec(srv->opts.prec);
     o.hbm_limit = 0;
     st = bqc_df_build(srv->ctx, basis, &o, (bqc_stream_t)s, &df);
   }
@@ -316,9 +323,10 @@ using namespace bqc;
 
 extern "C" {
 
-size_t bqc_serve_footprint(int nbf, int naux, int nocc) {
-  if (nbf <= 0 || naux <= 0 || nocc <= 0) return 0;
-  return serve_footprint(nbf, naux, nocc, true);
+size_t bqc_serve_footprint(int nbf, int naux, int nocc, int prec) {
+  if (nbf <= 0 || naux <= 0 || nocc <= 0 || prec < BQC_PREC_FP64 || prec > BQC_PREC_MIXED_F16X3)
+    return 0;
+  return serve_footprint(nbf, naux, nocc, shadow_of_prec(prec));
 }
 
 int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out) {
@@ -390,7 +398,7 @@ int bqc_serve_submit(bqc_server *srv, const bqc_request *q, uint64_t *ticket) {
   r->naux = nf[1];
   r->nocc = zsum / 2;
   r->footprint = serve_footprint(r->nbf, r->naux, std::max(1, r->nocc),
-                                 srv->opts.prec != BQC_PREC_FP64);
+                                 shadow_of_prec(srv->opts.prec));
   if (r->footprint > srv->budget) return BQC_E_ADMISSION;
   std::lock_guard<std::mutex> lk(srv->mu);
   r->id = srv->next_id++;

@@ -17,10 +17,12 @@
 // records an error code in the context's device flag and skips its work.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "bqc_internal.h"
 #include "df_internal.h"
@@ -48,8 +50,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 // fp32 tensor map, rank 2 or 3, 128-byte swizzle; dims/box innermost first;
 // strides in bytes for dims 1.. (rank-1 entries).
+static int make_tmap(CUtensorMap *map, CUtensorMapDataType dtype, const void *base, int rank,
+                     const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box);
+
 int make_tmap_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                   const uint64_t *strides_bytes, const uint32_t *box) {
+  return make_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, base, rank, dims, strides_bytes, box);
+}
+
+// fp16 tensor map with the same conventions (boxes of 64 elements = 128 bytes).
+static int make_tmap_f16(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                         const uint64_t *strides_bytes, const uint32_t *box) {
+  return make_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, base, rank, dims, strides_bytes, box);
+}
+
+static int make_tmap(CUtensorMap *map, CUtensorMapDataType dtype, const void *base, int rank,
+                     const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box) {
   auto enc = get_encode();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled unavailable", __FILE__, __LINE__);
@@ -67,7 +83,7 @@ int make_tmap_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *
     b[i] = box[i];
   }
   for (int i = 0; i < rank - 1; ++i) s[i] = strides_bytes[i];
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base),
+  CUresult r = enc(map, dtype, (cuuint32_t)rank, const_cast<void *>(base),
                    d, s, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -116,6 +132,20 @@ constexpr int kGroupKb = 4;   // k-blocks (of 32) per TMEM chain: X pass (contra
 constexpr int kGroupKbS = 4;  // SYRK (contraction Naux x nocc)
 constexpr int kGroupKbT = 2;  // TRMM (contraction Naux)
 
+// Power-of-two scales of the FP16 split (written on the device by
+// k_scales for each build, read by the X-pass and SYRK epilogues).  FP16 has
+// TF32's 11-bit significand but a narrow exponent range (normal numbers from
+// 2^-14 to 65504), so every operand is scaled to a largest magnitude of at
+// most 2^14 before it is split: B by s_B (fixed at setup), C by s_C, X by
+// s_X.  Powers of two make the scaling and unscaling exact.
+struct MixScale {
+  float x_out;       // s_X / (s_B s_C): X-pass accumulator -> scaled X
+  float x_unscale;   // 1 / (s_B s_C): X-pass accumulator -> X
+  float c_scale;     // s_C
+  float pad;
+  double k_unscale;  // 1 / s_X^2: SYRK accumulator -> K
+};
+
 struct XpassParams {
   int64_t rows;      // Naux * N  (M of the GEMM)
   int n;             // N (rows per aux function)
@@ -125,6 +155,8 @@ struct XpassParams {
   int stages;
   int64_t tiles;     // row tiles x ncg
   float *Xh, *Xl;    // rows x ldx (TF32 hi / lo parts)
+  __half *Xh16, *Xl16;      // rows x ldx (FP16 hi / lo parts of s_X X), KIND f16
+  const MixScale *scale;    // KIND f16
   const float *Cf;   // N x ldx, fp32 C_occ
   float *wpart;      // [2 * ncg][rows] partial w per row
   int *flag;
@@ -137,12 +169,16 @@ struct XpassParams {
 
 // Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
 // t / ncg, column group t % ncg), so neighbouring CTAs share A rows in L2.
-// EPI 0: X[row][i] (hi/lo) and the fused w_P partials; EPI 1: X^T layout.
-template <int XN, int SPLIT, int EPI>
+// EPI 0: X[row][i] (hi/lo) and the fused w_P partials; EPI 1: X^T layout
+// (TF32 only).  KIND: TF32 or FP16 operands (k-blocks of 32 or 64 elements).
+template <int KIND, int XN, int SPLIT, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_xpass_tf32(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
-                 const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
-                 const XpassParams p) {
+    k_xpass(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+            const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
+            const XpassParams p) {
+  static_assert(KIND == kKindTF32 || EPI == 0, "the transposed epilogue is TF32 only");
+  using KD = Kind<KIND>;
+  constexpr int KE = KD::kElems;
   constexpr int HALF = XN / 2;
   constexpr int NS = SPLIT == 3 ? 2 : 1;  // operand parts per side
   constexpr uint32_t a_bytes = kAStage, c_bytes = XN * 128;
@@ -194,16 +230,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a = sbase + s * stage_bytes;  // [Ah][Al][Ch][Cl]
           const uint32_t bar = full0 + 8 * s;
           mbar_arrive_expect_tx(bar, stage_bytes);
-          tma_load_2d(a, &mapAh, bar, kb * 32, (int)m0);
-          if (SPLIT == 3) tma_load_2d(a + a_bytes, &mapAl, bar, kb * 32, (int)m0);
-          tma_load_2d(a + NS * a_bytes, &mapCh, bar, kb * 32, c0);
-          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, &mapCl, bar, kb * 32, c0);
+          tma_load_2d(a, &mapAh, bar, kb * KE, (int)m0);
+          if (SPLIT == 3) tma_load_2d(a + a_bytes, &mapAl, bar, kb * KE, (int)m0);
+          tma_load_2d(a + NS * a_bytes, &mapCh, bar, kb * KE, c0);
+          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, &mapCl, bar, kb * KE, c0);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(kBM, XN);
+      constexpr uint32_t idesc = KD::idesc(kBM, XN);
       int64_t kg = 0, g = 0;
       for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
         for (int gr = 0; gr < ngroups && ok; ++gr, ++g) {
@@ -227,17 +263,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4) {
                 const uint32_t acc = ((kb - kb0) | k4) != 0;
-                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(cl + k4 * 32), idesc, acc);
-                mma_tf32(d, sdesc_sw128(al + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, 1);
+                KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(cl + k4 * 32), acc, idesc);
+                KD::mma(d, sdesc_sw128(al + k4 * 32), sdesc_sw128(ch + k4 * 32), 1, idesc);
               }
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4)
-                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, 1);
+                KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), 1, idesc);
             } else {
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4) {
                 const uint32_t acc = ((kb - kb0) | k4) != 0;
-                mma_tf32(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), idesc, acc);
+                KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), acc, idesc);
               }
             }
             mma_commit(empty0 + 8 * s);
@@ -274,7 +310,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
       const int64_t row = m0 + q * 32 + lane;
-      if (EPI == 0 && ok && row < p.rows) {
+      if (KIND == kKindF16 && ok && row < p.rows) {
+        // scaled X split into FP16 hi + lo (each rounded to nearest), and the
+        // fused w partial sum_i X[row][i] C[mu][i] of the unscaled X
+        const float xo = p.scale->x_out, xu = p.scale->x_unscale;
+        const int mu = (int)(row % p.n);
+        const int col = cg * XN + h * HALF;
+        __half *xh = p.Xh16 + row * p.ldx + col;
+        __half *xl = p.Xl16 + row * p.ldx + col;
+        const float *cr = p.Cf + (int64_t)mu * p.ldx + col;
+        float wsum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < HALF; c += 8) {
+          const float4 ca = *reinterpret_cast<const float4 *>(cr + c);
+          const float4 cb = *reinterpret_cast<const float4 *>(cr + c + 4);
+          wsum = fmaf(acc[c], ca.x, wsum);
+          wsum = fmaf(acc[c + 1], ca.y, wsum);
+          wsum = fmaf(acc[c + 2], ca.z, wsum);
+          wsum = fmaf(acc[c + 3], ca.w, wsum);
+          wsum = fmaf(acc[c + 4], cb.x, wsum);
+          wsum = fmaf(acc[c + 5], cb.y, wsum);
+          wsum = fmaf(acc[c + 6], cb.z, wsum);
+          wsum = fmaf(acc[c + 7], cb.w, wsum);
+          __align__(16) __half hv[8], lv[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float v = acc[c + k] * xo;
+            hv[k] = __float2half_rn(v);
+            lv[k] = __float2half_rn(v - __half2float(hv[k]));
+          }
+          *reinterpret_cast<uint4 *>(xh + c) = *reinterpret_cast<const uint4 *>(hv);
+          *reinterpret_cast<uint4 *>(xl + c) = *reinterpret_cast<const uint4 *>(lv);
+        }
+        p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum * xu;
+      }
+      if (KIND == kKindTF32 && EPI == 0 && ok && row < p.rows) {
         const int mu = (int)(row % p.n);
         const int col = cg * XN + h * HALF;
         float *xh = p.Xh + row * p.ldx + col;
@@ -304,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum;
       }
-      if (EPI == 1 && ok && row < p.rows && (int)(row % p.bk) < p.bkv) {
+      if (KIND == kKindTF32 && EPI == 1 && ok && row < p.rows && (int)(row % p.bk) < p.bkv) {
         // consecutive lanes hold consecutive q of one mu: coalesced per column
         const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
         const int col = cg * XN + h * HALF;
@@ -350,10 +420,11 @@ struct SyrkParams {
   int n, ldx, naux;
   int ntri;
   int nchunk, p_per_chunk;
-  int nib;       // ldx / 32
+  int nib;       // k-blocks per aux function: ceil(ldx / elements per k-block)
   int stages;
   double *part;  // [chunk][ntri][128][128]
   int *flag;
+  const MixScale *scale;  // KIND f16: partial tiles are unscaled by 1 / s_X^2
   // blocked operand mode (direct mode): Y^T stored as [P block][i][mu][32];
   // rows mu, K = (i, P) with k-block kb = i * npb + P block; chunks are ranges
   // of kb_per_chunk k-blocks of kb_total
@@ -375,11 +446,14 @@ constexpr int kSyCols = kBM / (kEpiWarps / 4);  // columns per epilogue thread
 constexpr uint32_t kLoCol = 2 * kBM;             // TMEM columns of the compensation term
 
 // Persistent SYRK over work items (lower tile, aux chunk); item i -> tile
-// i % ntri, chunk i / ntri.  Partial tiles are written in FP64.
-template <int SPLIT>
+// i % ntri, chunk i / ntri.  Partial tiles are written in FP64.  KIND: TF32
+// or FP16 operands (the blocked operand mode of direct mode is TF32 only).
+template <int KIND, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_syrk_tf32(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
-                const SyrkParams p) {
+    k_syrk(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
+           const SyrkParams p) {
+  using KD = Kind<KIND>;
+  constexpr int KE = KD::kElems;
   constexpr int NS = SPLIT == 3 ? 2 : 1;
   constexpr uint32_t stage_bytes = NS * 2 * kAStage;  // [Xh(tm)][Xh(tn)][Xl(tm)][Xl(tn)]
   extern __shared__ uint8_t smem_raw[];
@@ -445,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_4d(a + 3 * kAStage, &mapXl, bar, 0, tn * kBM, ii, pb);
             }
           } else {
-            const int P = (int)P0 + kb / p.nib, i0 = (kb % p.nib) * 32;
+            const int P = (int)P0 + kb / p.nib, i0 = (kb % p.nib) * KE;
             tma_load_3d(a, &mapXh, bar, i0, tm * kBM, P);
             tma_load_3d(a + kAStage, &mapXh, bar, i0, tn * kBM, P);
             if (SPLIT == 3) {
@@ -458,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(kBM, kBM);
+      constexpr uint32_t idesc = KD::idesc(kBM, kBM);
       int64_t kg = 0, g = 0;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int nkb;
@@ -482,17 +556,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4) {
                 const uint32_t acc = ((kb - kb0) | k4) != 0;
-                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(ln + k4 * 32), idesc, acc);
-                mma_tf32(d, sdesc_sw128(lm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, 1);
+                KD::mma(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(ln + k4 * 32), acc, idesc);
+                KD::mma(d, sdesc_sw128(lm + k4 * 32), sdesc_sw128(hn + k4 * 32), 1, idesc);
               }
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4)
-                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, 1);
+                KD::mma(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), 1, idesc);
             } else {
 #pragma unroll
               for (int k4 = 0; k4 < 4; ++k4) {
                 const uint32_t acc = ((kb - kb0) | k4) != 0;
-                mma_tf32(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), idesc, acc);
+                KD::mma(d, sdesc_sw128(hm + k4 * 32), sdesc_sw128(hn + k4 * 32), acc, idesc);
               }
             }
             mma_commit(empty0 + 8 * s);
@@ -548,14 +622,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       double *dst =
           p.part + (((int64_t)(it / p.ntri) * p.ntri + it % p.ntri) * kBM + r) * kBM + h * kSyCols;
       const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+      const double ku = (KIND == kKindF16) ? p.scale->k_unscale : 1.0;
 #pragma unroll
       for (int c = 0; c < kSyCols; c += 16) {
         float lo[16];
         tmem_ld16(tl + c, lo);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-          const double2 v = make_double2(ok ? (double)hi[c + i] + (double)lo[i] : 0.0,
-                                         ok ? (double)hi[c + i + 1] + (double)lo[i + 1] : 0.0);
+          const double2 v =
+              make_double2(ok ? ((double)hi[c + i] + (double)lo[i]) * ku : 0.0,
+                           ok ? ((double)hi[c + i + 1] + (double)lo[i + 1]) * ku : 0.0);
           *reinterpret_cast<double2 *>(dst + c + i) = v;
         }
       }
@@ -874,12 +950,145 @@ __global__ void k_expand_split(const double *__restrict__ B, int n, int ld, int6
   if (Bl) Bl[i] = l;
 }
 
+// ------------------------------------------------------- FP16 split prep ---
+
+// atomicMax on non-negative floats through their bit patterns (order-preserving).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned *addr, float v) {
+  atomicMax(addr, __float_as_uint(v));
+}
+
+// *out = max |a[i]| over n doubles (as the bits of a float; *out zeroed before).
+__global__ void __launch_bounds__(256) k_absmax_f64(const double *__restrict__ a, int64_t n,
+                                                    unsigned *out) {
+  float m = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, (float)fabs(a[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// B (FP64 packed lower triangle) -> scaled full-square FP16 split shadows:
+// f = s_B B, Bh = fp16(f), Bl = fp16(f - Bh), rows zero-padded to ld.
+__global__ void k_expand_split16(const double *__restrict__ B, int n, int ld, int64_t npair,
+                                 int np, float sB, __half *__restrict__ Bh,
+                                 __half *__restrict__ Bl) {
+  const int64_t nn = (int64_t)n * ld;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn * np) return;
+  const int64_t P = i / nn, rc = i % nn;
+  const int64_t r = rc / ld, c = rc % ld;
+  float h = 0.0f, l = 0.0f;
+  if (c < n) {
+    const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
+    const float f = (float)(B[P * npair + hi * (hi + 1) / 2 + lo] * (double)sB);
+    h = __half2float(__float2half_rn(f));
+    l = f - h;
+  }
+  Bh[i] = __float2half_rn(h);
+  Bl[i] = __float2half_rn(l);
+}
+
+// *out = max over rows of sum_c Bh[row][c]^2 (one warp per row; float bits).
+__global__ void __launch_bounds__(256) k_rowsq_max16(const __half *__restrict__ Bh, int64_t rows,
+                                                     int ld, unsigned *out) {
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  float best = 0.0f;
+  for (int64_t r = w0; r < rows; r += nw) {
+    const __half *row = Bh + r * ld;
+    float s = 0.0f;
+    for (int c = lane; c < ld; c += 32) {
+      const float v = __half2float(row[c]);
+      s = fmaf(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    best = fmaxf(best, s);
+  }
+  if (lane == 0) atomic_max_nonneg(out, best);
+}
+
+// Per-build statistics of C_occ (N x nocc, row-major): st[0] = bits of
+// max|C|, st[1 + i] = sum_nu C[nu][i]^2 (float, atomically accumulated; st
+// zeroed before).  Block b covers rows 32b .. 32b + 31.
+__global__ void __launch_bounds__(256) k_cstats(const double *__restrict__ C, int n, int nocc,
+                                                float *st) {
+  const int r0 = blockIdx.x * 32, r1 = min(n, r0 + 32);
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < nocc; i += blockDim.x) {
+    float sq = 0.0f;
+    for (int r = r0; r < r1; ++r) {
+      const float v = (float)C[(int64_t)r * nocc + i];
+      sq = fmaf(v, v, sq);
+      m = fmaxf(m, fabsf(v));
+    }
+    atomicAdd(st + 1 + i, sq);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<unsigned *>(st), m);
+}
+
+// Exponent e with x <= 2^e (x >= 0; 0 for x == 0).
+__device__ __forceinline__ int ceil_exp2(double x) {
+  if (!(x > 0.0)) return 0;
+  int e = 0;
+  const double m = frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
+  return m == 0.5 ? e - 1 : e;
+}
+
+// The build's scales (one thread): s_C = 2^(14 - e(max|C|)) and, from
+// |X_P,mu i| <= ||B_P,mu .||_2 ||C_. i||_2 (Cauchy-Schwarz), s_X = 2^(14 - e(bound))
+// with bound = rownorm * max_i ||C_. i||_2 * 1.01 (the factor covers the
+// float column sums).  s_B = 2^eB_scale was fixed at setup.
+__global__ void k_scales(const float *st, int nocc, int eB_scale, double rownorm,
+                         MixScale *out) {
+  if (threadIdx.x != 0) return;
+  const float maxc = __uint_as_float(reinterpret_cast<const unsigned *>(st)[0]);
+  float mc2 = 0.0f;
+  for (int i = 0; i < nocc; ++i) mc2 = fmaxf(mc2, st[1 + i]);
+  const int eC = 14 - ceil_exp2((double)maxc);
+  const int eX = 14 - ceil_exp2(rownorm * sqrt((double)mc2) * 1.01);
+  MixScale sc;
+  sc.c_scale = ldexpf(1.0f, eC);
+  sc.x_out = ldexpf(1.0f, eX - eB_scale - eC);
+  sc.x_unscale = ldexpf(1.0f, -eB_scale - eC);
+  sc.pad = 0.0f;
+  sc.k_unscale = ldexp(1.0, -2 * eX);
+  *out = sc;
+}
+
+// FP16 split of C_occ: Ch[i][nu] = fp16(s_C c), Cl = fp16(s_C c - Ch) with
+// c = C[nu][i] (zero padded to ldx x ld), and Cf[mu][i] = fp32 C (unscaled,
+// for the fused w).
+__global__ void k_prep_c16(const double *C, int n, int nocc, int ld, int ldx,
+                           const MixScale *sc, __half *Ch, __half *Cl, float *Cf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)ldx * ld;
+  if (i < tot) {
+    const int oi = (int)(i / ld), nu = (int)(i % ld);
+    float h = 0.0f, l = 0.0f;
+    if (oi < nocc && nu < n) {
+      const float f = (float)(C[(int64_t)nu * nocc + oi] * (double)sc->c_scale);
+      h = __half2float(__float2half_rn(f));
+      l = f - h;
+    }
+    Ch[i] = __float2half_rn(h);
+    Cl[i] = __float2half_rn(l);
+  }
+  if (i < (int64_t)n * ldx) {
+    const int mu = (int)(i / ldx), oi = (int)(i % ldx);
+    Cf[i] = oi < nocc ? (float)C[(int64_t)mu * nocc + oi] : 0.0f;
+  }
+}
+
 // ------------------------------------------------------------- driver ----
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct MixedPlan {
-  int ld;        // B shadow row length (N rounded to 4)
+  int ld;        // TF32 B shadow row length (N rounded to 4)
+  int ld16;      // FP16 B shadow row length (N rounded to 8: 16-byte rows)
   int ldx;       // X row length = ncg * xn
   int ncg, xn;   // X-pass column groups and tile width
   int xp_stages[2];   // [split1, split3]
@@ -894,10 +1103,13 @@ static MixedPlan mixed_plan(int n, int naux, int nocc, int nsm) {
   MixedPlan m;
   m.grid = nsm;
   m.ld = round_up(n, 4);
+  m.ld16 = round_up(n, 8);
   const int ldx0 = round_up(std::max(nocc, 1), 32);
   m.ncg = (ldx0 + 255) / 256;
   m.xn = round_up((ldx0 + m.ncg - 1) / m.ncg, 32);
   m.ldx = m.ncg * m.xn;
+  // a stage holds one 128-byte k-block row per operand tile row: the same
+  // bytes for TF32 (32 elements) and FP16 (64 elements)
   const size_t avail = 232448 - 1024 - 256;
   for (int k = 0; k < 2; ++k) {
     const size_t stage = (size_t)(k + 1) * (kAStage + (size_t)m.xn * 128);
@@ -934,86 +1146,201 @@ static MixedPlan mixed_plan(int n, int naux, int nocc, int nsm) {
   return m;
 }
 
-size_t mixed_workspace_bytes(int n, int naux, int nocc) {
+size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow) {
   const MixedPlan m = mixed_plan(n, naux, nocc, sm_count());
-  size_t b = (size_t)naux * n * m.ld * 4;            // Bl (Bh counted by the caller)
-  b += (size_t)naux * n * (2 * m.ldx - nocc) * 4;    // Xh padding + Xl (Xh counted by caller)
-  b += (size_t)2 * m.ldx * m.ld * 4 + (size_t)n * m.ldx * 4;
-  b += (size_t)2 * m.ncg * naux * n * 4 + (size_t)naux * 4;
-  b += (size_t)m.nchunk * m.ntri * kBM * kBM * 8;
+  size_t b = (size_t)2 * m.ncg * naux * n * 4 + (size_t)naux * 4;  // w partials, w32
+  b += (size_t)m.nchunk * m.ntri * kBM * kBM * 8;                    // SYRK partials
+  if (shadow == BQC_SHADOW_F16) {
+    b += (size_t)2 * naux * n * m.ld16 * 2;                          // Bh16, Bl16
+    b += (size_t)2 * naux * n * m.ldx * 2;                           // Xh16, Xl16
+    b += (size_t)2 * m.ldx * m.ld16 * 2 + (size_t)n * m.ldx * 4;     // C split, Cf
+    b += (size_t)(nocc + 1) * 4 + 256;                               // statistics, scales
+  } else {
+    b += (size_t)2 * naux * n * m.ld * 4;                            // Bh, Bl
+    b += (size_t)2 * naux * n * m.ldx * 4;                           // Xh, Xl
+    b += (size_t)2 * m.ldx * m.ld * 4 + (size_t)n * m.ldx * 4;       // C split, Cf
+  }
   return b;
 }
 
 struct MixedState {
   MixedPlan plan;
+  int shadow = BQC_SHADOW_TF32;
   CUtensorMap mapAh, mapAl, mapCh, mapCl, mapXh, mapXl;
   DBuf Bl, Xl, Cl, Cf, wpart, w32;
+  // FP16 split
+  DBuf Bh16, Bl16, Xh16, Xl16, Ch16, Cl16, cstat, scale;
+  int eB = 0;            // s_B = 2^eB
+  double rownorm = 0.0;  // max_{P,mu} ||B_P,mu .||_2, unscaled, with a safety factor
+  size_t bytes() const {
+    return Bl.n + Xl.n + Cl.n + Cf.n + wpart.n + w32.n + Bh16.n + Bl16.n + Xh16.n + Xl16.n +
+           Ch16.n + Cl16.n + cstat.n + scale.n;
+  }
 };
 
 void MixedDeleter::operator()(MixedState *p) const { delete p; }
+
+size_t mixed_bytes(const MixedState *ms) { return ms ? ms->bytes() : 0; }
 
 int mixed_ld(int n) { return round_up(n, 4); }
 
 #define BQC_XN_LIST(X) X(32) X(64) X(96) X(128) X(160) X(192) X(224) X(256)
 
-template <int XN, int SPLIT, int EPI>
+template <int KIND, int XN, int SPLIT, int EPI>
 static int xpass_run(size_t smem, const XpassParams *p, const CUtensorMap *Ah,
                      const CUtensorMap *Al, const CUtensorMap *Ch, const CUtensorMap *Cl, int grid,
                      cudaStream_t s) {
   if (!p) {
-    BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_tf32<XN, SPLIT, EPI>,
+    BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass<KIND, XN, SPLIT, EPI>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return BQC_OK;
   }
-  k_xpass_tf32<XN, SPLIT, EPI><<<grid, kThreads, smem, s>>>(*Ah, *Al, *Ch, *Cl, *p);
+  k_xpass<KIND, XN, SPLIT, EPI><<<grid, kThreads, smem, s>>>(*Ah, *Al, *Ch, *Cl, *p);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
 }
 
+// kind f16 exists only as the three-product split with the row epilogue.
 template <int XN>
-static int xpass_split_epi(int split, int epi, size_t smem, const XpassParams *p,
+static int xpass_split_epi(int kind, int split, int epi, size_t smem, const XpassParams *p,
                            const CUtensorMap *Ah, const CUtensorMap *Al, const CUtensorMap *Ch,
                            const CUtensorMap *Cl, int grid, cudaStream_t s) {
+  if (kind == kKindF16) {
+    if (split != 3 || epi != 0) return BQC_E_UNSUPPORTED;
+    return xpass_run<kKindF16, XN, 3, 0>(smem, p, Ah, Al, Ch, Cl, grid, s);
+  }
   if (split == 3)
-    return epi ? xpass_run<XN, 3, 1>(smem, p, Ah, Al, Ch, Cl, grid, s)
-               : xpass_run<XN, 3, 0>(smem, p, Ah, Al, Ch, Cl, grid, s);
-  return epi ? xpass_run<XN, 1, 1>(smem, p, Ah, Ah, Ch, Ch, grid, s)
-             : xpass_run<XN, 1, 0>(smem, p, Ah, Ah, Ch, Ch, grid, s);
+    return epi ? xpass_run<kKindTF32, XN, 3, 1>(smem, p, Ah, Al, Ch, Cl, grid, s)
+               : xpass_run<kKindTF32, XN, 3, 0>(smem, p, Ah, Al, Ch, Cl, grid, s);
+  return epi ? xpass_run<kKindTF32, XN, 1, 1>(smem, p, Ah, Ah, Ch, Ch, grid, s)
+             : xpass_run<kKindTF32, XN, 1, 0>(smem, p, Ah, Ah, Ch, Ch, grid, s);
 }
 
 // p == nullptr: only set the kernel's shared-memory attribute.
-static int dispatch_xn(int xn, int split, int epi, size_t smem, const XpassParams *p,
+static int dispatch_xn(int xn, int kind, int split, int epi, size_t smem, const XpassParams *p,
                        const CUtensorMap *Ah, const CUtensorMap *Al, const CUtensorMap *Ch,
                        const CUtensorMap *Cl, int grid, cudaStream_t s) {
 #define BQC_XN_CASE(V) \
   case V:              \
-    return xpass_split_epi<V>(split, epi, smem, p, Ah, Al, Ch, Cl, grid, s);
+    return xpass_split_epi<V>(kind, split, epi, smem, p, Ah, Al, Ch, Cl, grid, s);
   switch (xn) { BQC_XN_LIST(BQC_XN_CASE) }
 #undef BQC_XN_CASE
   return BQC_E_UNSUPPORTED;
 }
 
-int mixed_setup(Df *df, cudaStream_t s) {
+static int make_side_stream(Df *df, cudaStream_t s) {
+  if (df->side) return BQC_OK;
+  // the side stream inherits the caller's priority (serving ranks requests by it)
+  int prio = 0;
+  if (s && cudaStreamGetPriority(s, &prio) != cudaSuccess) {
+    cudaGetLastError();
+    prio = 0;
+  }
+  BQC_CUDA_TRY(cudaStreamCreateWithPriority(&df->side, cudaStreamNonBlocking, prio));
+  BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork, cudaEventDisableTiming));
+  BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
+  return BQC_OK;
+}
+
+// FP16 split shadows of the stored B: the scale s_B from max|B| and the
+// largest row norm of B (for the per-build bound on |X|), read back once.
+static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
+  const Basis *b = df->basis;
+  const int n = b->nbf, naux = b->naux;
+  const MixedPlan &m = ms->plan;
+  Ctx *ctx = df->ctx;
+  DBuf stat;
+  BQC_TRY(stat.alloc(ctx, 256));
+  BQC_CUDA_TRY(cudaMemsetAsync(stat.p, 0, 256, s));
+  const int64_t nb = (int64_t)naux * df->npair;
+  const unsigned grid = (unsigned)std::min<int64_t>((nb + 255) / 256, (int64_t)sm_count() * 8);
+  k_absmax_f64<<<std::max(1u, grid), 256, 0, s>>>(df->B64.as<double>(), nb, stat.as<unsigned>());
+  BQC_LAUNCH_CHECK();
+  unsigned hb = 0;
+  BQC_CUDA_TRY(cudaMemcpyAsync(&hb, stat.p, 4, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  float maxb = 0.0f;
+  std::memcpy(&maxb, &hb, 4);
+  int e = 0;
+  if (maxb > 0.0f) {
+    const double mt = std::frexp((double)maxb, &e);
+    if (mt == 0.5) --e;
+  }
+  ms->eB = 14 - e;
+  const float sB = std::ldexp(1.0f, ms->eB);
+  BQC_TRY(ms->Bh16.alloc(ctx, (size_t)naux * n * m.ld16 * 2));
+  BQC_TRY(ms->Bl16.alloc(ctx, (size_t)naux * n * m.ld16 * 2));
+  {
+    const int64_t tot = (int64_t)n * m.ld16 * naux;
+    k_expand_split16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        df->B64.as<double>(), n, m.ld16, df->npair, naux, sB, ms->Bh16.as<__half>(),
+        ms->Bl16.as<__half>());
+    BQC_LAUNCH_CHECK();
+  }
+  BQC_CUDA_TRY(cudaMemsetAsync(stat.p, 0, 256, s));
+  k_rowsq_max16<<<(unsigned)sm_count() * 8, 256, 0, s>>>(ms->Bh16.as<__half>(), (int64_t)naux * n,
+                                                         m.ld16, stat.as<unsigned>());
+  BQC_LAUNCH_CHECK();
+  BQC_CUDA_TRY(cudaMemcpyAsync(&hb, stat.p, 4, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  float maxsq = 0.0f;
+  std::memcpy(&maxsq, &hb, 4);
+  // |B row| <= |Bh row| / (1 - 2^-11); the factor also covers the float sums
+  ms->rownorm = std::sqrt((double)maxsq) / (double)sB * (1.0 + 1.0 / 256.0);
+  BQC_TRY(ms->Xh16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
+  BQC_TRY(ms->Xl16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
+  BQC_TRY(ms->Ch16.alloc(ctx, (size_t)m.ldx * m.ld16 * 2));
+  BQC_TRY(ms->Cl16.alloc(ctx, (size_t)m.ldx * m.ld16 * 2));
+  BQC_TRY(ms->cstat.alloc(ctx, (size_t)(b->nocc + 1) * 4));
+  BQC_TRY(ms->scale.alloc(ctx, sizeof(MixScale)));
+  {  // A operands: B shadows as (Naux*N) rows x ld16 columns
+    const uint64_t dims[2] = {(uint64_t)m.ld16, (uint64_t)naux * n};
+    const uint64_t str[1] = {(uint64_t)m.ld16 * 2};
+    const uint32_t box[2] = {64, kBM};
+    BQC_TRY(make_tmap_f16(&ms->mapAh, ms->Bh16.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f16(&ms->mapAl, ms->Bl16.p, 2, dims, str, box));
+  }
+  {  // B operands: C^T split as ldx rows x ld16 columns, boxes of xn rows
+    const uint64_t dims[2] = {(uint64_t)m.ld16, (uint64_t)m.ldx};
+    const uint64_t str[1] = {(uint64_t)m.ld16 * 2};
+    const uint32_t box[2] = {64, (uint32_t)m.xn};
+    BQC_TRY(make_tmap_f16(&ms->mapCh, ms->Ch16.p, 2, dims, str, box));
+    BQC_TRY(make_tmap_f16(&ms->mapCl, ms->Cl16.p, 2, dims, str, box));
+  }
+  {  // X split as (ldx, N, Naux)
+    const uint64_t dims[3] = {(uint64_t)m.ldx, (uint64_t)n, (uint64_t)naux};
+    const uint64_t str[2] = {(uint64_t)m.ldx * 2, (uint64_t)n * m.ldx * 2};
+    const uint32_t box[3] = {64, kBM, 1};
+    BQC_TRY(make_tmap_f16(&ms->mapXh, ms->Xh16.p, 3, dims, str, box));
+    BQC_TRY(make_tmap_f16(&ms->mapXl, ms->Xl16.p, 3, dims, str, box));
+  }
+  BQC_TRY(dispatch_xn(m.xn, kKindF16, 3, 0, m.xp_smem[1], nullptr, nullptr, nullptr, nullptr,
+                      nullptr, 0, s));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk<kKindF16, 3>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m.sy_smem[1]));
+  return BQC_OK;
+}
+
+int mixed_setup(Df *df, int shadow, cudaStream_t s) {
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux, no = b->nocc;
   MixedState *ms = new MixedState();
   df->mixed.reset(ms);
+  ms->shadow = shadow;
   ms->plan = mixed_plan(n, naux, no, sm_count());
   const MixedPlan &m = ms->plan;
   if (m.xp_stages[1] < 2 || m.sy_stages[1] < 2) return BQC_E_UNSUPPORTED;
-  if (!df->side) {
-    // the side stream inherits the caller's priority (serving ranks requests by it)
-    int prio = 0;
-    if (s && cudaStreamGetPriority(s, &prio) != cudaSuccess) {
-      cudaGetLastError();
-      prio = 0;
-    }
-    BQC_CUDA_TRY(cudaStreamCreateWithPriority(&df->side, cudaStreamNonBlocking, prio));
-    BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork, cudaEventDisableTiming));
-    BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
-  }
+  BQC_TRY(make_side_stream(df, s));
   Ctx *ctx = df->ctx;
-  // split shadow of B (Bh lives in df->B32, allocated by the caller)
+  BQC_TRY(ms->Cf.alloc(ctx, (size_t)n * m.ldx * 4));
+  BQC_TRY(ms->wpart.alloc(ctx, (size_t)2 * m.ncg * naux * n * 4));
+  BQC_TRY(ms->w32.alloc(ctx, (size_t)naux * 4));
+  BQC_TRY(df->Kpart.alloc(ctx, (size_t)m.nchunk * m.ntri * kBM * kBM * 8));
+  if (!df->Jp.p) BQC_TRY(df->Jp.alloc(ctx, (size_t)df->npair * 8));
+  if (shadow == BQC_SHADOW_F16) return mixed_setup_f16(df, ms, s);
+  // TF32 split shadow of B (Bh lives in df->B32)
+  BQC_TRY(df->B32.alloc(ctx, (size_t)naux * n * m.ld * 4));
   BQC_TRY(ms->Bl.alloc(ctx, (size_t)naux * n * m.ld * 4));
   {
     const int64_t tot = (int64_t)n * m.ld * naux;
@@ -1025,11 +1352,6 @@ int mixed_setup(Df *df, cudaStream_t s) {
   BQC_TRY(ms->Xl.alloc(ctx, (size_t)naux * n * m.ldx * 4));
   BQC_TRY(df->Ct32.alloc(ctx, (size_t)m.ldx * m.ld * 4));
   BQC_TRY(ms->Cl.alloc(ctx, (size_t)m.ldx * m.ld * 4));
-  BQC_TRY(ms->Cf.alloc(ctx, (size_t)n * m.ldx * 4));
-  BQC_TRY(ms->wpart.alloc(ctx, (size_t)2 * m.ncg * naux * n * 4));
-  BQC_TRY(ms->w32.alloc(ctx, (size_t)naux * 4));
-  BQC_TRY(df->Kpart.alloc(ctx, (size_t)m.nchunk * m.ntri * kBM * kBM * 8));
-  if (!df->Jp.p) BQC_TRY(df->Jp.alloc(ctx, (size_t)df->npair * 8));
   {  // A operands: B shadows as (Naux*N) rows x ld columns
     const uint64_t dims[2] = {(uint64_t)m.ld, (uint64_t)naux * n};
     const uint64_t str[1] = {(uint64_t)m.ld * 4};
@@ -1053,42 +1375,63 @@ int mixed_setup(Df *df, cudaStream_t s) {
   }
   for (int k = 0; k < 2; ++k)
     for (int epi = 0; epi < 2; ++epi)
-      BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, epi, m.xp_smem[k], nullptr, nullptr, nullptr, nullptr,
-                          nullptr, 0, s));
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      BQC_TRY(dispatch_xn(m.xn, kKindTF32, k ? 3 : 1, epi, m.xp_smem[k], nullptr, nullptr,
+                          nullptr, nullptr, nullptr, 0, s));
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk<kKindTF32, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)m.sy_smem[0]));
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk<kKindTF32, 3>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)m.sy_smem[1]));
   return BQC_OK;
 }
 
-// X pass over `rows` rows of the A operands (Ah, Al), writing Xh / Xl and,
-// if w_out, the Coulomb contraction w.
-int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtensorMap *Ah,
-                const CUtensorMap *Al, int64_t rows, float *Xh, float *Xl, double *w_out) {
+// X pass over `rows` rows of the A operands, writing the X split (TF32 into
+// Xh / Xl, FP16 into the state's Xh16 / Xl16) and, if w_out, the Coulomb
+// contraction w.
+static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_t s,
+                       const CUtensorMap *Ah, const CUtensorMap *Al, int64_t rows, float *Xh,
+                       float *Xl, double *w_out) {
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, no = b->nocc;
-  const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld, (int64_t)n * m.ldx);
   df->mark(0, s);
-  k_prep_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, n, no, m.ld, m.ldx,
-                                                          df->Ct32.as<float>(),
-                                                          split == 3 ? ms->Cl.as<float>() : nullptr,
-                                                          ms->Cf.as<float>());
-  BQC_LAUNCH_CHECK();
+  if (kind == kKindF16) {
+    const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld16, (int64_t)n * m.ldx);
+    BQC_CUDA_TRY(cudaMemsetAsync(ms->cstat.p, 0, ms->cstat.n, s));
+    k_cstats<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(C, n, no, ms->cstat.as<float>());
+    BQC_LAUNCH_CHECK();
+    k_scales<<<1, 32, 0, s>>>(ms->cstat.as<float>(), no, ms->eB, ms->rownorm,
+                              ms->scale.as<MixScale>());
+    BQC_LAUNCH_CHECK();
+    k_prep_c16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        C, n, no, m.ld16, m.ldx, ms->scale.as<MixScale>(), ms->Ch16.as<__half>(),
+        ms->Cl16.as<__half>(), ms->Cf.as<float>());
+    BQC_LAUNCH_CHECK();
+  } else {
+    const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld, (int64_t)n * m.ldx);
+    k_prep_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        C, n, no, m.ld, m.ldx, df->Ct32.as<float>(), split == 3 ? ms->Cl.as<float>() : nullptr,
+        ms->Cf.as<float>());
+    BQC_LAUNCH_CHECK();
+  }
   df->mark(1, s);
   XpassParams p;
   p.rows = rows;
   p.n = n;
   p.ldx = m.ldx;
   p.ncg = m.ncg;
-  p.kblocks = (m.ld + 31) / 32;
+  const int ke = kind == kKindF16 ? 64 : 32;
+  p.kblocks = ((kind == kKindF16 ? m.ld16 : m.ld) + ke - 1) / ke;
   const int k = split == 3 ? 1 : 0;
   p.stages = m.xp_stages[k];
   p.tiles = (rows + kBM - 1) / kBM * m.ncg;
   p.Xh = Xh;
   p.Xl = Xl;
+  p.Xh16 = kind == kKindF16 ? ms->Xh16.as<__half>() : nullptr;
+  p.Xl16 = kind == kKindF16 ? ms->Xl16.as<__half>() : nullptr;
+  p.scale = kind == kKindF16 ? ms->scale.as<MixScale>() : nullptr;
   p.Cf = ms->Cf.as<float>();
   p.wpart = ms->wpart.as<float>();
   p.flag = df->ctx->flag;
@@ -1097,7 +1440,8 @@ int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtens
   p.q0 = 0;
   p.bkv = 0;
   p.xrows = 0;
-  BQC_TRY(dispatch_xn(m.xn, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl, grid, s));
+  BQC_TRY(dispatch_xn(m.xn, kind, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl,
+                      grid, s));
   if (w_out) {
     k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
                                                     w_out, ms->w32.as<float>());
@@ -1106,8 +1450,8 @@ int mixed_xpass(Df *df, const double *C, int split, cudaStream_t s, const CUtens
   return BQC_OK;
 }
 
-int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, int naux, double *K,
-               cudaStream_t s) {
+static int mixed_syrk(Df *df, int kind, int split, const CUtensorMap *Xh, const CUtensorMap *Xl,
+                      int naux, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const int n = df->basis->nbf;
@@ -1118,20 +1462,24 @@ int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, 
   q.ntri = m.ntri;
   q.p_per_chunk = m.ppc;
   q.nchunk = (naux + m.ppc - 1) / m.ppc;
-  q.nib = m.ldx / 32;
+  const int ke = kind == kKindF16 ? 64 : 32;
+  q.nib = (m.ldx + ke - 1) / ke;
   const int k = split == 3 ? 1 : 0;
   q.stages = m.sy_stages[k];
   q.part = df->Kpart.as<double>();
   q.flag = df->ctx->flag;
+  q.scale = kind == kKindF16 ? ms->scale.as<MixScale>() : nullptr;
   q.mode2d = 0;
   q.npb = 0;
   q.kb_total = 0;
   q.kb_per_chunk = 0;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
-  if (split == 3)
-    k_syrk_tf32<3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
+  if (kind == kKindF16)
+    k_syrk<kKindF16, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
+  else if (split == 3)
+    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
   else
-    k_syrk_tf32<1><<<grid, kThreads, m.sy_smem[0], s>>>(*Xh, *Xh, q);
+    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(*Xh, *Xh, q);
   BQC_LAUNCH_CHECK();
   k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(df->Kpart.as<double>(), q.nchunk,
                                                                   m.ntri, n, K);
@@ -1139,25 +1487,33 @@ int mixed_syrk(Df *df, int split, const CUtensorMap *Xh, const CUtensorMap *Xl, 
   return BQC_OK;
 }
 
-// w comes fused from the X pass in both mixed precisions (FP32 row partials
+// w comes fused from the X pass in every mixed precision (FP32 row partials
 // of X C, summed in FP64).  The J pass then runs on the side stream,
-// concurrently with the SYRK: 3xTF32 reads the packed FP64 B (FP64 FMAs),
-// single-pass TF32 reads the TF32 shadow.  Reading B in FP64 matters: with
-// the TF32 split of B in the J pass, max|dJ| is only ~1e-6, but in a diffuse
-// basis the orthogonalisation amplifies it (by up to 1/sqrt(s_min)) into a
-// DIIS error of ~1e-4, which would set the mixed SCF's error floor; the
-// error of the fused w, a smooth Coulomb-like perturbation, stays ~1e-7.
+// concurrently with the SYRK: 3xTF32 and FP16x3 read the packed FP64 B
+// (FP64 FMAs), single-pass TF32 reads the TF32 shadow.  Reading B in FP64
+// matters: with the split of B in the J pass, max|dJ| is only ~1e-6, but in a
+// diffuse basis the orthogonalisation amplifies it (by up to 1/sqrt(s_min))
+// into a DIIS error of ~1e-4, which would set the mixed SCF's error floor;
+// the error of the fused w, a smooth Coulomb-like perturbation, stays ~1e-7.
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   if (!ms) return BQC_E_INVALID;
-  const int split = prec == BQC_PREC_MIXED_TF32X3 ? 3 : 1;
+  const int kind = prec == BQC_PREC_MIXED_F16X3 ? kKindF16 : kKindTF32;
+  if ((kind == kKindF16) != (ms->shadow == BQC_SHADOW_F16)) {
+    set_error(kind == kKindF16 ? "MIXED_F16X3 needs FP16 shadows (BQC_SHADOW_F16)"
+                               : "TF32 precisions need TF32 shadows (BQC_SHADOW_TF32)",
+              __FILE__, __LINE__);
+    return BQC_E_INVALID;
+  }
+  const int split = prec == BQC_PREC_MIXED_TF32 ? 1 : 3;
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux;
   const int64_t rows = (int64_t)naux * n;
   const bool j64 = split == 3 && df->B64.p;
-  BQC_TRY(mixed_xpass(df, C, split, s, &ms->mapAh, &ms->mapAl, rows, df->X32.as<float>(),
-                      ms->Xl.as<float>(), df->w.as<double>()));
+  BQC_TRY(mixed_xpass(df, C, kind, split, s, &ms->mapAh, &ms->mapAl, rows,
+                      kind == kKindF16 ? nullptr : df->X32.as<float>(),
+                      kind == kKindF16 ? nullptr : ms->Xl.as<float>(), df->w.as<double>()));
   df->mark(2, s);
   df->j_from = 2;
   cudaStream_t js = s;
@@ -1179,7 +1535,7 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     BQC_LAUNCH_CHECK();
   }
   if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
-  BQC_TRY(mixed_syrk(df, split, &ms->mapXh, &ms->mapXl, naux, K, s));
+  BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, s));
   df->mark(3, s);
   if (df->side) {
     BQC_CUDA_TRY(cudaEventRecord(df->join, df->side));
@@ -1377,15 +1733,17 @@ int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s) {
     BQC_TRY(make_tmap_f32(&dm->mapYl, dm->Xl.p, 4, dims, str, box));
   }
   for (int k = 0; k < 2; ++k)
-    BQC_TRY(dispatch_xn(m.xn, k ? 3 : 1, 1, m.xp_smem[k], nullptr, nullptr, nullptr, nullptr,
-                        nullptr, 0, s));
+    BQC_TRY(dispatch_xn(m.xn, kKindTF32, k ? 3 : 1, 1, m.xp_smem[k], nullptr, nullptr, nullptr,
+                        nullptr, nullptr, 0, s));
   BQC_CUDA_TRY(cudaFuncSetAttribute(k_trmm_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)dm->tr_smem[0]));
   BQC_CUDA_TRY(cudaFuncSetAttribute(k_trmm_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)dm->tr_smem[1]));
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk<kKindTF32, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)m.sy_smem[0]));
-  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk<kKindTF32, 3>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)m.sy_smem[1]));
   return BQC_OK;
 }
@@ -1434,8 +1792,11 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
     p.bkv = nv;
     p.xrows = (int64_t)n * m.ldx;
     const int grid = (int)std::min<int64_t>(m.grid, p.tiles);
-    BQC_TRY(dispatch_xn(m.xn, split, 1, m.xp_smem[k], &p, &dm->mapRh, &dm->mapRl, &dm->mapCh,
-                        &dm->mapCl, grid, s));
+    p.Xh16 = nullptr;
+    p.Xl16 = nullptr;
+    p.scale = nullptr;
+    BQC_TRY(dispatch_xn(m.xn, kKindTF32, split, 1, m.xp_smem[k], &p, &dm->mapRh, &dm->mapRl,
+                        &dm->mapCh, &dm->mapCl, grid, s));
   }
   return BQC_OK;
 }
@@ -1478,11 +1839,12 @@ int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
   q.npb = dm->naux_ld / 32;
   q.kb_total = dm->kb_total;
   q.kb_per_chunk = dm->sy_kbpc;
+  q.scale = nullptr;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
   if (split == 3)
-    k_syrk_tf32<3><<<grid, kThreads, m.sy_smem[1], s>>>(dm->mapYh, dm->mapYl, q);
+    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(dm->mapYh, dm->mapYl, q);
   else
-    k_syrk_tf32<1><<<grid, kThreads, m.sy_smem[0], s>>>(dm->mapYh, dm->mapYh, q);
+    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(dm->mapYh, dm->mapYh, q);
   BQC_LAUNCH_CHECK();
   k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(dm->Kpart.as<double>(),
                                                                   q.nchunk, m.ntri, n, K);

@@ -1,5 +1,6 @@
 // Blackwell (sm_103a) building blocks in inline PTX: mbarriers with bounded
-// waits, TMA tiled loads, tcgen05 MMA (kind::tf32, cta_group::1), TMEM
+// waits, TMA tiled loads, tcgen05 MMA (kind::tf32 and kind::f16,
+// cta_group::1), TMEM
 // allocation and loads, and the shared-memory / instruction descriptors.
 #pragma once
 #include <cuda.h>
@@ -127,6 +128,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       : "memory");
 }
 
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (A and B both FP16),
+// FP32 accumulate.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive on `bar` once all MMAs issued so far by this thread have completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
@@ -184,6 +196,34 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
          | (2u << 10)              // B format: tf32
          | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// Instruction descriptor, kind::f16: D f32, A/B f16 (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4)                 // D format: f32
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Operand kinds of the mixed-precision GEMMs.  A k-block is one 128-byte
+// swizzled row of an operand tile: 32 TF32 or 64 FP16 elements, consumed by
+// four MMAs of 32 bytes of K each (K = 8 for tf32, K = 16 for f16).
+enum { kKindTF32 = 0, kKindF16 = 1 };
+template <int KIND> struct Kind;
+template <> struct Kind<kKindTF32> {
+  static constexpr int kElems = 32;
+  __device__ static __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
+                                             uint32_t idesc) {
+    mma_tf32(d, a, b, idesc, acc);
+  }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) { return idesc_tf32(M, N); }
+};
+template <> struct Kind<kKindF16> {
+  static constexpr int kElems = 64;
+  __device__ static __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
+                                             uint32_t idesc) {
+    mma_f16(d, a, b, idesc, acc);
+  }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) { return idesc_f16(M, N); }
+};
 
 }  // namespace tc
 }  // namespace bqc

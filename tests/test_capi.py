@@ -41,6 +41,11 @@ def test_status_strings(lib):
 
 def test_footprint_is_monotone(lib):
     import paper_2502_17963_gb300 as bqc
-    a = lib.bqc_serve_footprint(100, 300, 20)
-    b = lib.bqc_serve_footprint(200, 600, 40)
-    assert b >= a
+    for prec in range(4):
+        a = lib.bqc_serve_footprint(100, 300, 20, prec)
+        b = lib.bqc_serve_footprint(200, 600, 40, prec)
+        assert b >= a > 0
+    # FP16 split shadows take half the bytes of the TF32 ones; FP64 needs none
+    f64, tf, f16 = (lib.bqc_serve_footprint(800, 2400, 160, p) for p in (0, 2, 3))
+    assert f64 < f16 < tf
+    assert lib.bqc_serve_footprint(100, 300, 20, 7) == 0

@@ -14,7 +14,11 @@ KA = sum_P |X_P|(|B_P||C|)^T + transpose) times 1e-11.  3xTF32: K within
 2^-14 KA (the bound of the other mixed tests); J reads the FP64 B, so its
 error is the fused w's, bounded by 2^-18 sum_P |B_P| wa_P with
 wa_P = sum_mu,i (|B_P||C|)_mu i |C|_mu i (three TF32 products per term, FP32
-accumulation in short chains).
+accumulation in short chains).  Every elementwise bound carries an absolute
+floor of 1e-11: the library's stored mode screens (P|mu nu) below 1e-12 to
+exactly zero, so at orbital pairs whose integrals are all below that the
+contraction scales are themselves ~1e-12 and the screened remainder
+(measured 1e-12 in J) is the whole difference.
 """
 import numpy as np
 import pytest
@@ -65,7 +69,7 @@ def test_full_jk_w32_fp64(w32):
           f"max|dK| {dK.max():.3e} (ratio {(dK / w32['KA']).max():.3e}), "
           f"max|J| {np.abs(w32['Jo']).max():.3e}, max|K| {np.abs(w32['Ko']).max():.3e}")
     assert dJ.max() < 1e-10 and dK.max() < 1e-10
-    assert (dJ <= 1e-11 * w32["JA"]).all() and (dK <= 1e-11 * w32["KA"]).all()
+    assert (dJ <= 1e-11 * w32["JA"] + 1e-11).all() and (dK <= 1e-11 * w32["KA"] + 1e-11).all()
 
 
 def test_full_jk_w32_mixed_tf32x3(w32):
@@ -73,9 +77,26 @@ def test_full_jk_w32_mixed_tf32x3(w32):
     J, K = df.jk(w32["Cg"], bqc.PREC_MIXED_TF32X3)
     assert (J - J.T).abs().max().item() == 0.0 and (K - K.T).abs().max().item() == 0.0
     J, K = J.cpu().numpy(), K.cpu().numpy()
+    _check_mixed(w32, J, K, "3xTF32")
+
+
+def _check_mixed(w32, J, K, label):
     dJ, dK = np.abs(J - w32["Jo"]), np.abs(K - w32["Ko"])
-    rK, rJ = (dK / w32["KA"]).max(), (dJ / w32["JW"]).max()
-    print(f"w32 3xTF32: max|dK| {dK.max():.3e} (ratio to KA {rK:.3e}), max|dJ| {dJ.max():.3e} "
-          f"(ratio to JW {rJ:.3e})")
+    rK = (dK / (w32["KA"] + 2.0 ** 14 * 1e-11)).max()
+    rJ = (dJ / (w32["JW"] + 2.0 ** 18 * 1e-11)).max()
+    big = w32["JW"] > 1e-6
+    print(f"w32 {label}: max|dK| {dK.max():.3e} (ratio to KA {rK:.3e}), max|dJ| {dJ.max():.3e} "
+          f"(ratio to JW {rJ:.3e}; {(dJ[big] / w32['JW'][big]).max():.3e} where JW > 1e-6)")
     assert rK < 2.0 ** -14
     assert rJ < 2.0 ** -18
+
+
+def test_full_jk_w32_mixed_f16x3(w32):
+    """The same full comparison for split FP16 (its own DF handle with FP16
+    shadows, the benchmark's precision)."""
+    bqc, basis = w32["bqc"], w32["basis"]
+    d16 = bqc.DF(w32["df"].ctx, basis, mode=bqc.DF_STORED, keep_fp32=bqc.SHADOW_F16)
+    J, K = d16.jk(w32["Cg"], bqc.PREC_MIXED_F16X3)
+    assert (J - J.T).abs().max().item() == 0.0 and (K - K.T).abs().max().item() == 0.0
+    _check_mixed(w32, J.cpu().numpy(), K.cpu().numpy(), "F16X3")
+    d16.close()
