@@ -64,6 +64,11 @@ def parse():
                     help="--scf: anchored incremental FP64 stage")
     ap.add_argument("--direct", action="store_true",
                     help="direct (on-the-fly) DF run, default (H2O)_128")
+    ap.add_argument("--screen-ablation", action="store_true",
+                    help="time the three survivor compactions of the screened 3-centre "
+                         "integrals on one aux block of (H2O)_128 (default) at tau = 1e-10")
+    ap.add_argument("--mp2", action="store_true",
+                    help="DF-MP2 energy after an SCF at --waters (default (H2O)_16)")
     return ap.parse_args()
 
 
@@ -439,10 +444,110 @@ def staged_scf_check(bqc, ctx, df, torch, prec):
             "_C": rs["C"][:, :no].contiguous()}
 
 
+def run_screen_ablation(args):
+    """One aux block of 1024 functions of the direct-mode integrals, computed
+    with each survivor compaction (0 sorted prefix, 1 the paper's warp loop
+    buffer, 2 a two-kernel global index list): CUDA-event time per variant
+    (median of 3 after a warm-up), and a bitwise comparison of the outputs."""
+    import torch
+
+    import paper_2502_17963_gb300 as bqc
+    import workload
+    from paper_2502_17963_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    nw = args.waters if args.waters != 64 else 128
+    mol = workload.water_cluster(nw)
+    ctx = bqc.Context(0)
+    basis = bqc.Basis(ctx, mol)
+    df = bqc.DF(ctx, basis, mode=bqc.DF_DIRECT, schwarz=1e-10, aux_block=1024, keep_fp32=False)
+    p1 = min(1024, basis.naux)
+    outs, times = [], {}
+    names = {0: "sorted_prefix", 1: "warp_loop_buffer", 2: "global_index_list"}
+    stream = torch.cuda.current_stream()
+    for v in range(3):
+        out = torch.zeros((p1, basis.npair), dtype=torch.float64, device="cuda")
+        df.int3c_screened(0, p1, v, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            df.int3c_screened(0, p1, v, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        times[names[v]] = statistics.median(ts)
+        outs.append(out.cpu() if v == 0 else out)
+    same = [bool(torch.equal(outs[v].cpu(), outs[0])) for v in (1, 2)]
+    cand, kept = df.screening()
+    line = {"metric": "ms per screened 3-centre integral block", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{mol.name} aux functions [0, {p1}) of Naux={basis.naux}, "
+                                   f"N={basis.nbf}, Schwarz 1e-10 (direct-mode block)"},
+            "ms": times, "bitwise_equal_to_sorted_prefix": same,
+            "triplets_kept_fraction_all_aux": kept / max(1, cand),
+            "speed_vs_sorted_prefix": {k: times["sorted_prefix"] / v for k, v in times.items()}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mp2(args):
+    """DF-MP2 (FP64 DFMA path) after a staged SCF: seconds, flop rate against
+    the FP64 peak, and the energy."""
+    import torch
+
+    import paper_2502_17963_gb300 as bqc
+    import workload
+    from paper_2502_17963_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    nw = args.waters if args.waters != 64 else 16
+    mol = workload.water_cluster(nw)
+    ctx = bqc.Context(0)
+    basis = bqc.Basis(ctx, mol)
+    df = bqc.DF(ctx, basis, mode=bqc.DF_STORED, keep_fp32=bqc.SHADOW_F16)
+    r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_F16X3, incremental=True, keep_arrays=True)
+    C, eps = r["C"].contiguous(), r["eps"].contiguous()
+    bqc.mp2(df, C, eps)  # warm
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index(0))
+    clocks.start()
+    t0 = time.perf_counter()
+    e2 = bqc.mp2(df, C, eps)
+    dt = time.perf_counter() - t0
+    clk = clocks.stop()
+    n, naux, no = basis.nbf, basis.naux, basis.nocc
+    nv = r["nmo"] - no
+    bi = max(1, min(16, no, int((1 << 27) ** 0.5 / max(1, nv))))
+    pair_flops = 0.0
+    for i0 in range(0, no, bi):
+        ni = min(bi, no - i0)
+        for j0 in range(0, i0 + 1, bi):
+            nj = min(bi, no - j0)
+            pair_flops += 2.0 * ni * nv * nj * nv * naux
+    flops = 2.0 * naux * n * n * no + 2.0 * naux * n * no * nv + pair_flops
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 DFMA units per SM at the max SM clock
+    line = {"metric": "s per DF-MP2 energy (FP64)", "value": dt, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": f"{mol.name} DF-MP2 after the staged SCF, N={n}, Naux={naux}, "
+                                   f"nocc={no}, nvir={nv}"},
+            "e2_Eh": e2, "e_scf_Eh": r["energy"],
+            "roofline": {"bound": "alu", "achieved": flops / dt / 1e12, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp64_peak,
+                         "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                         "algorithmic_flop": flops},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.serve:
         return run_serve(args)
+    if args.screen_ablation:
+        return run_screen_ablation(args)
+    if args.mp2:
+        return run_mp2(args)
     if args.direct:
         return run_direct(args)
     if args.scf:

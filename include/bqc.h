@@ -156,6 +156,8 @@ typedef struct {
   int keep_fp32;       /* split shadows of B for the mixed precisions: one of
                           BQC_SHADOW_NONE / _TF32 / _F16 (default TF32)       */
   size_t hbm_limit;    /* AUTO: choose DIRECT when STORED needs more (0 = free memory) */
+  int aux_begin;       /* stored mode: keep only the rows P in [aux_begin, aux_end) */
+  int aux_end;         /* of B (an aux shard); 0, 0 = every aux function         */
 } bqc_df_opts;
 
 /* Build the DF machinery (Sec. 2.2).  STORED: metric, Cholesky, raw (Q|mu nu),
@@ -173,9 +175,40 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
 int bqc_df_destroy(bqc_df *df);
 /* Mode actually built and bytes of device memory held. */
 int bqc_df_info(const bqc_df *df, int *mode, size_t *device_bytes);
+/* Aux shards (the per-GPU partition of the CD-ERIs, Sec. 2.2.2 and the
+ * multi-GPU scaling of Sec. 3.2, applied to the aux index).  J and K are
+ * sums over P of per-P terms, so a handle built with
+ * opts.aux_begin/aux_end = [P0, P1) holds only the rows P0 <= P < P1 of B,
+ * and bqc_jk on it returns the partial J and K of those rows; the partials
+ * of shards that cover [0, Naux) once add up to the full J and K (one
+ * all-reduce per Fock build across the processes that hold them).  The rows
+ * of B = L^-1 (Q|mu nu) up to P1 need the integrals of every Q < P1, so the
+ * build solves rows [0, P1) and keeps its own (the one-GPU construction; a
+ * multi-GPU build would solve pair-column slices and exchange them once).
+ * bqc_scf_run and bqc_mp2 need the whole tensor and refuse a shard
+ * (BQC_E_INVALID); direct mode has no shards (BQC_E_UNSUPPORTED).  This
+ * call returns the handle's range ([0, Naux) for a whole tensor). */
+int bqc_df_shard(const bqc_df *df, int *aux_begin, int *aux_end);
 /* Schwarz screening of the 3-centre integrals (Sec. 2.2): shell triplets
  * (aux shell, orbital shell pair) considered and kept (Q_P Q_mu nu >= tau). */
 int bqc_df_screening(const bqc_df *df, int64_t *candidates, int64_t *survivors);
+/* Survivor compaction of the screened three-centre integrals, as a
+ * measured choice (the paper's GPU prescreening, Sec. 2.2.1 and Algorithm 1,
+ * against the alternatives it discusses).  Writes (P|mu nu) for the aux
+ * functions [p0, p1) into out_dev ((p1 - p0) x Npair, packed as bqc_int3c),
+ * with the handle's Schwarz screening; screened entries are left untouched
+ * (zero the buffer first).  variant 0: the library's compaction (pairs
+ * sorted by Schwarz factor, survivors a prefix per aux shell, dense
+ * triplet index, no divergence); 1: the paper's per-warp loop buffer
+ * (screen 32 candidates per warp, append survivors to a 64-entry ring in
+ * shared memory, compute a warp's worth at a time); 2: a screening kernel
+ * that appends survivors to a global index list, then a kernel over the
+ * list.  All three compute the same triplets with the same arithmetic, so
+ * their outputs are identical.  Async except variant 2, which allocates the
+ * list from the context and synchronises the stream before releasing it. */
+int bqc_int3c_screened(const bqc_df *df, int p0, int p1, int variant, double *out_dev,
+                       bqc_stream_t stream);
+
 /* Copy B (Naux x Npair packed, FP64, stored mode) into a device buffer; or
  * the Cholesky factor L (Naux x Naux, lower, zeros above) when which = 1.  Async. */
 int bqc_df_copy(const bqc_df *df, int which, double *out_dev, bqc_stream_t stream);

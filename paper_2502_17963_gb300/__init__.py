@@ -48,7 +48,8 @@ class bqc_shell(ctypes.Structure):
 class bqc_df_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("schwarz", ctypes.c_double),
                 ("aux_block", ctypes.c_int), ("keep_fp32", ctypes.c_int),
-                ("hbm_limit", ctypes.c_size_t)]
+                ("hbm_limit", ctypes.c_size_t), ("aux_begin", ctypes.c_int),
+                ("aux_end", ctypes.c_int)]
 
 
 class bqc_scf_opts(ctypes.Structure):
@@ -117,8 +118,10 @@ _SIGS = {
     "bqc_df_build": (ip, [vp, vp, ctypes.POINTER(bqc_df_opts), vp, ctypes.POINTER(vp)]),
     "bqc_df_destroy": (ip, [vp]),
     "bqc_df_info": (ip, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
+    "bqc_df_shard": (ip, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bqc_df_screening": (ip, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "bqc_df_copy": (ip, [vp, ip, vp, vp]),
+    "bqc_int3c_screened": (ip, [vp, ip, ip, ip, vp, vp]),
     "bqc_jk": (ip, [vp, vp, ip, ip, vp, vp, vp]),
     "bqc_jk_host": (ip, [vp, vp, ip, ip, vp, vp, vp]),
     "bqc_jk_fp64_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp, vp]),
@@ -318,13 +321,16 @@ class DF:
     """bqc_df: the density-fitting tensor (stored) or its on-the-fly machinery (direct)."""
 
     def __init__(self, ctx: Context, basis: Basis, mode: int = DF_STORED, schwarz: float = -1.0,
-                 aux_block: int = 1024, keep_fp32=True, hbm_limit: int = 0, stream=None):
+                 aux_block: int = 1024, keep_fp32=True, hbm_limit: int = 0, stream=None,
+                 aux_range=None):
         """keep_fp32: True / SHADOW_TF32 (split TF32 shadows), SHADOW_F16 (split
-        FP16 shadows, for PREC_MIXED_F16X3), False / SHADOW_NONE (FP64 only)."""
+        FP16 shadows, for PREC_MIXED_F16X3), False / SHADOW_NONE (FP64 only).
+        aux_range: (P0, P1) to hold only that aux shard of B (stored mode)."""
         self.ctx, self.basis = ctx, basis
         shadow = SHADOW_TF32 if keep_fp32 is True else (SHADOW_NONE if keep_fp32 is False
                                                           else int(keep_fp32))
-        o = bqc_df_opts(mode, schwarz, aux_block, shadow, hbm_limit)
+        p0, p1 = aux_range if aux_range is not None else (0, 0)
+        o = bqc_df_opts(mode, schwarz, aux_block, shadow, hbm_limit, p0, p1)
         h = vp()
         check(lib().bqc_df_build(ctx.h, basis.h, ctypes.byref(o), _stream_ptr(stream),
                                  ctypes.byref(h)), "bqc_df_build")
@@ -332,6 +338,9 @@ class DF:
         m, b = ctypes.c_int(), ctypes.c_size_t()
         check(lib().bqc_df_info(h, ctypes.byref(m), ctypes.byref(b)), "bqc_df_info")
         self.mode, self.device_bytes = m.value, b.value
+        a0, a1 = ctypes.c_int(), ctypes.c_int()
+        check(lib().bqc_df_shard(h, ctypes.byref(a0), ctypes.byref(a1)), "bqc_df_shard")
+        self.aux_range = (a0.value, a1.value)
 
     def screening(self):
         """(shell triplets considered, kept) by the Schwarz screening."""
@@ -339,9 +348,19 @@ class DF:
         check(lib().bqc_df_screening(self.h, ctypes.byref(c), ctypes.byref(k)), "bqc_df_screening")
         return c.value, k.value
 
+    def int3c_screened(self, p0: int, p1: int, variant: int = 0, out=None, stream=None):
+        """(P|mu nu) for aux functions [p0, p1) with this handle's screening and
+        the chosen survivor compaction (0 sorted prefix, 1 loop buffer, 2 list)."""
+        import torch
+        if out is None:
+            out = torch.zeros((p1 - p0, self.basis.npair), dtype=torch.float64, device="cuda")
+        check(lib().bqc_int3c_screened(self.h, p0, p1, variant, _ptr(out), _stream_ptr(stream)),
+              "bqc_int3c_screened")
+        return out
+
     def copy(self, which: int = 0, stream=None):
         """B (Naux, Npair) for which=0, the Cholesky factor L (Naux, Naux) for which=1."""
-        shape = (self.basis.naux, self.basis.npair) if which == 0 else \
+        shape = (self.aux_range[1] - self.aux_range[0], self.basis.npair) if which == 0 else \
             (self.basis.naux, self.basis.naux)
         out = _empty(shape)
         check(lib().bqc_df_copy(self.h, which, _ptr(out), _stream_ptr(stream)), "bqc_df_copy")

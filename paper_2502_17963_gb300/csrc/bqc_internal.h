@@ -153,6 +153,7 @@ struct Eri3cPlan {
   DBuf d_pairs_sorted;  // int2 per pair, sorted within class
   DBuf d_qpair_sorted;  // double per pair
   DBuf d_qaux;          // double per aux shell
+  DBuf d_qpair;         // double per pair, in the basis' (unsorted) pair order
   DBuf d_prefix;        // per (pair class, aux l): n_aux(l)+1 int64 prefix
   int64_t prefix_off[kNPairClass][kMaxLAux + 1] = {{0}};
   int64_t total[kNPairClass][kMaxLAux + 1] = {{0}};
@@ -166,6 +167,10 @@ int eri3c_plan(const Basis *b, double tau, const double *V_diag_dev, cudaStream_
 // packed lower triangle; screened-out entries are left untouched.
 int launch_eri3c(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *out,
                  int64_t ld, cudaStream_t s);
+// The same with a choice of survivor compaction (0: sorted prefix, the
+// default; 1: per-warp loop buffer; 2: two-kernel global index list).
+int launch_eri3c_variant(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *out,
+                         int64_t ld, int variant, cudaStream_t s);
 
 // --------------------------------------------------------- linalg ------
 

@@ -117,7 +117,7 @@ __global__ void k_unpack_sym(const double *Jp, int n, double *J) {
 }
 
 int jpass_fp64(Df *df, double *J, cudaStream_t s) {
-  const int n = df->basis->nbf, naux = df->basis->naux;
+  const int n = df->basis->nbf, naux = df->naux_loc;
   const int64_t npair = df->npair;
   if (!df->B64.p) return BQC_E_INVALID;
   const int sp = jpass_split(npair, naux);
@@ -133,7 +133,7 @@ int jpass_fp64(Df *df, double *J, cudaStream_t s) {
 
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {
   const Basis *b = df->basis;
-  const int n = b->nbf, naux = b->naux, no = b->nocc;
+  const int n = b->nbf, naux = df->naux_loc, no = b->nocc;
   const int64_t npair = df->npair;
   double *X = df->X64.as<double>();
   df->mark(0, s);
@@ -207,6 +207,8 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
   o.aux_block = 1024;
   o.keep_fp32 = 1;
   o.hbm_limit = 0;
+  o.aux_begin = 0;
+  o.aux_end = 0;
   if (opts) o = *opts;
   cudaStream_t s = (cudaStream_t)stream;
   const int n = basis->nbf, naux = basis->naux, no = basis->nocc;
@@ -223,6 +225,18 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
   }
   if (mode != BQC_DF_STORED && mode != BQC_DF_DIRECT) return BQC_E_INVALID;
   if (o.keep_fp32 < BQC_SHADOW_NONE || o.keep_fp32 > BQC_SHADOW_F16) return BQC_E_INVALID;
+  // aux shard [P0, P1) (stored mode): both 0 selects every aux function
+  int P0 = o.aux_begin, P1 = o.aux_end;
+  if (P0 == 0 && P1 == 0) P1 = naux;
+  if (P0 < 0 || P1 > naux || P0 >= P1) {
+    set_error("bqc_df_build: aux shard outside [0, Naux) or empty", __FILE__, __LINE__);
+    return BQC_E_INVALID;
+  }
+  const bool shard = P0 != 0 || P1 != naux;
+  if (shard && mode != BQC_DF_STORED) {
+    set_error("bqc_df_build: aux shards are a stored-mode feature", __FILE__, __LINE__);
+    return BQC_E_UNSUPPORTED;
+  }
   if (o.schwarz < 0.0) o.schwarz = (mode == BQC_DF_STORED) ? 1e-12 : 1e-10;
   if (o.aux_block <= 0) o.aux_block = 1024;
   bqc_df *df = new (std::nothrow) bqc_df();
@@ -232,6 +246,8 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
   df->mode = mode;
   df->npair = npair;
   df->opts = o;
+  df->p0 = P0;
+  df->naux_loc = P1 - P0;
   auto fail = [&](int st) {
     cudaStreamSynchronize(s);
     delete df;
@@ -252,16 +268,43 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
   if ((st = df->w.alloc(ctx, (size_t)naux * 8)) != BQC_OK) return fail(st);
   if (mode == BQC_DF_STORED) {
     df->Vdiag.release();  // metric only needed for the screening plan
-    if ((st = df->B64.alloc(ctx, (size_t)naux * npair * 8)) != BQC_OK) return fail(st);
-    if (cudaMemsetAsync(df->B64.p, 0, (size_t)naux * npair * 8, s) != cudaSuccess)
-      return fail(BQC_E_CUDA);
-    if ((st = launch_eri3c(basis, &df->plan, 0, naux, df->B64.as<double>(), npair, s)) != BQC_OK)
-      return fail(st);
-    if ((st = trsm_lower_left(ctx, df->L.as<double>(), naux, df->B64.as<double>(), npair, npair,
-                              s)) != BQC_OK)
-      return fail(st);
-    if ((st = df->X64.alloc(ctx, (size_t)naux * n * no * 8)) != BQC_OK) return fail(st);
-    if ((st = df->Jp.alloc(ctx, (size_t)jpass_split(npair, naux) * npair * 8)) != BQC_OK)
+    if (!shard) {
+      if ((st = df->B64.alloc(ctx, (size_t)naux * npair * 8)) != BQC_OK) return fail(st);
+      if (cudaMemsetAsync(df->B64.p, 0, (size_t)naux * npair * 8, s) != cudaSuccess)
+        return fail(BQC_E_CUDA);
+      if ((st = launch_eri3c(basis, &df->plan, 0, naux, df->B64.as<double>(), npair, s)) !=
+          BQC_OK)
+        return fail(st);
+      if ((st = trsm_lower_left(ctx, df->L.as<double>(), naux, df->B64.as<double>(), npair,
+                                npair, s)) != BQC_OK)
+        return fail(st);
+    } else {
+      // B_P for P in [P0, P1) depends on (Q|mu nu) for every Q <= P (the
+      // triangular solve couples them): solve rows [0, P1) with the leading
+      // P1 x P1 block of L and keep the shard's rows
+      DBuf raw, Lb;
+      if ((st = raw.alloc(ctx, (size_t)P1 * npair * 8)) != BQC_OK) return fail(st);
+      if (cudaMemsetAsync(raw.p, 0, (size_t)P1 * npair * 8, s) != cudaSuccess)
+        return fail(BQC_E_CUDA);
+      if ((st = launch_eri3c(basis, &df->plan, 0, P1, raw.as<double>(), npair, s)) != BQC_OK)
+        return fail(st);
+      if ((st = Lb.alloc(ctx, (size_t)P1 * P1 * 8)) != BQC_OK) return fail(st);
+      if (cudaMemcpy2DAsync(Lb.p, (size_t)P1 * 8, df->L.p, (size_t)naux * 8, (size_t)P1 * 8, P1,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(BQC_E_CUDA);
+      if ((st = trsm_lower_left(ctx, Lb.as<double>(), P1, raw.as<double>(), npair, npair, s)) !=
+          BQC_OK)
+        return fail(st);
+      if ((st = df->B64.alloc(ctx, (size_t)(P1 - P0) * npair * 8)) != BQC_OK) return fail(st);
+      if (cudaMemcpyAsync(df->B64.p, raw.as<double>() + (size_t)P0 * npair,
+                          (size_t)(P1 - P0) * npair * 8, cudaMemcpyDeviceToDevice,
+                          s) != cudaSuccess)
+        return fail(BQC_E_CUDA);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return fail(BQC_E_CUDA);
+    }
+    const int nl = df->naux_loc;
+    if ((st = df->X64.alloc(ctx, (size_t)nl * n * no * 8)) != BQC_OK) return fail(st);
+    if ((st = df->Jp.alloc(ctx, (size_t)jpass_split(npair, nl) * npair * 8)) != BQC_OK)
       return fail(st);
     if (o.keep_fp32 != BQC_SHADOW_NONE)
       if ((st = mixed_setup(df, o.keep_fp32, s)) != BQC_OK) return fail(st);
@@ -288,6 +331,13 @@ int bqc_df_info(const bqc_df *df, int *mode, size_t *bytes) {
   return BQC_OK;
 }
 
+int bqc_df_shard(const bqc_df *df, int *aux_begin, int *aux_end) {
+  if (!df) return BQC_E_INVALID;
+  if (aux_begin) *aux_begin = df->p0;
+  if (aux_end) *aux_end = df->p0 + df->naux_loc;
+  return BQC_OK;
+}
+
 int bqc_df_screening(const bqc_df *df, int64_t *candidates, int64_t *survivors) {
   if (!df) return BQC_E_INVALID;
   if (candidates) *candidates = df->plan.candidates;
@@ -301,7 +351,7 @@ int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
   const int naux = df->basis->naux;
   if (which == 0) {
     if (df->mode != BQC_DF_STORED) return BQC_E_INVALID;
-    BQC_CUDA_TRY(cudaMemcpyAsync(out, df->B64.p, (size_t)naux * df->npair * 8,
+    BQC_CUDA_TRY(cudaMemcpyAsync(out, df->B64.p, (size_t)df->naux_loc * df->npair * 8,
                                  cudaMemcpyDeviceToDevice, s));
   } else if (which == 1) {
     BQC_CUDA_TRY(
@@ -310,6 +360,15 @@ int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
     return BQC_E_INVALID;
   }
   return BQC_OK;
+}
+
+int bqc_int3c_screened(const bqc_df *df, int p0, int p1, int variant, double *out,
+                       bqc_stream_t stream) {
+  if (!df || !out || variant < 0 || variant > 2) return BQC_E_INVALID;
+  if (p0 < 0 || p1 > df->basis->naux || p0 >= p1) return BQC_E_INVALID;
+  BQC_CUDA_TRY(cudaSetDevice(df->ctx->device));
+  return launch_eri3c_variant(df->basis, &df->plan, p0, p1, out, df->npair, variant,
+                              (cudaStream_t)stream);
 }
 
 int bqc_df_timing(bqc_df *df, int enable) {

@@ -22,6 +22,9 @@ struct Df {
   int mode = BQC_DF_STORED;
   int64_t npair = 0;
   bqc_df_opts opts{};
+  int p0 = 0;        // first aux function of the handle's shard
+  int naux_loc = 0;  // aux functions held (Naux unless the handle is a shard)
+  bool is_shard() const { return naux_loc != basis->naux; }
   DBuf L;      // Naux x Naux lower Cholesky factor of the metric
   DBuf Vdiag;  // metric copy (screening; direct mode keeps it)
   Eri3cPlan plan;
@@ -68,6 +71,7 @@ struct Df {
     return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +
            wpart.n + Kpart.n + raw.n + Linv.n + Xraw.n + gamma.n + D2.n +
            plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n +
+           plan.d_qpair.n +
            mixed_bytes(mixed.get());
   }
 };

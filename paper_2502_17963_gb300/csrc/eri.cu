@@ -512,8 +512,57 @@ struct Eri3cArgs {
   int64_t ld;
   int *flag;
   int64_t out_elems;
+  // screening-ablation variants (ring buffer, index list): the class's pairs
+  // in their original order with their Schwarz factors, the aux-shell factors
+  const int2 *pairs_orig;
+  const double *qpair_orig;
+  const double *qaux;
+  double tau;
+  int np;
+  int64_t *list;           // index-list variant: survivors (capacity n_aux * np)
+  unsigned long long *count;
 };
 
+// One shell triplet (P | a b) by a group of G lanes (gl = lane in the group),
+// written into the packed output; inactive groups compute a copy of a valid
+// triplet (so the warp stays convergent) and write nothing.
+template <int LC, int LA, int LB>
+__device__ __forceinline__ void eri3c_triplet(const Eri3cArgs &a, double *scr, int gl, int Pi,
+                                              int2 pr, bool active) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G;
+  const ShellRef sc = load_shell(a.aux, Pi);
+  const ShellRef sa = load_shell(a.orb, pr.x);
+  const ShellRef sb = load_shell(a.orb, pr.y);
+  const double *res = os_quartet<LA, LB, LC, 0, G>(
+      a.boys, scr, gl, sa, a.orb.exps + sa.poff, a.orb.coefs + sa.poff, &sb,
+      a.orb.exps + sb.poff, a.orb.coefs + sb.poff, sc, a.aux.exps + sc.poff,
+      a.aux.coefs + sc.poff, nullptr, nullptr, nullptr);
+  if (active) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC);
+    const bool diag = pr.x == pr.y;
+    for (int idx = gl; idx < O::NOUT; idx += G) {
+      const int ic = idx % NC;
+      const int ab = idx / NC;
+      const int ib = ab % NB, ia = ab / NB;
+      const int P = sc.fn + ic;
+      if (P < a.p0 || P >= a.p1) continue;
+      int mu = sa.fn + ia, nu = sb.fn + ib;
+      if (diag && mu < nu) continue;
+      if (mu < nu) { const int t2 = mu; mu = nu; nu = t2; }
+      const int64_t col = (int64_t)mu * (mu + 1) / 2 + nu;
+      const int64_t o = (int64_t)(P - a.p0) * a.ld + col;
+      if (o < 0 || o >= a.out_elems) { atomicExch(a.flag, 3); continue; }
+      a.out[o] = res[idx] * c_cnorm[ncum(LA) + ia] * c_cnorm[ncum(LB) + ib] *
+                 c_cnorm[ncum(LC) + ic];
+    }
+  }
+}
+
+// Shipped compaction: pairs of a class sorted by decreasing Schwarz factor,
+// so the survivors of aux shell P are the prefix [0, cut_P) of the list; the
+// scanned cuts map a dense triplet index t onto (P, pair) by binary search,
+// and every lane computes a surviving triplet (no test, no divergence).
 template <int LC, int LA, int LB>
 __global__ void __launch_bounds__(256) k_eri3c(Eri3cArgs a) {
   using O = Os<LA, LB, LC, 0>;
@@ -543,36 +592,135 @@ __global__ void __launch_bounds__(256) k_eri3c(Eri3cArgs a) {
       const int mid = (lo + hi) >> 1;
       if (a.prefix[mid] <= t) lo = mid; else hi = mid;
     }
-    const int Pi = a.aux_list[lo];
-    const int2 pr = a.pairs[t - a.prefix[lo]];
-    const ShellRef sc = load_shell(a.aux, Pi);
-    const ShellRef sa = load_shell(a.orb, pr.x);
-    const ShellRef sb = load_shell(a.orb, pr.y);
-    const double *res = os_quartet<LA, LB, LC, 0, G>(
-        a.boys, scr, gl, sa, a.orb.exps + sa.poff, a.orb.coefs + sa.poff, &sb,
-        a.orb.exps + sb.poff, a.orb.coefs + sb.poff, sc, a.aux.exps + sc.poff,
-        a.aux.coefs + sc.poff, nullptr, nullptr, nullptr);
-    if (active) {
-      constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC);
-      const bool diag = pr.x == pr.y;
-      for (int idx = gl; idx < O::NOUT; idx += G) {
-        const int ic = idx % NC;
-        const int ab = idx / NC;
-        const int ib = ab % NB, ia = ab / NB;
-        const int P = sc.fn + ic;
-        if (P < a.p0 || P >= a.p1) continue;
-        int mu = sa.fn + ia, nu = sb.fn + ib;
-        if (diag && mu < nu) continue;
-        if (mu < nu) { const int t2 = mu; mu = nu; nu = t2; }
-        const int64_t col = (int64_t)mu * (mu + 1) / 2 + nu;
-        const int64_t o = (int64_t)(P - a.p0) * a.ld + col;
-        if (o < 0 || o >= a.out_elems) { atomicExch(a.flag, 3); continue; }
-        a.out[o] = res[idx] * c_cnorm[ncum(LA) + ia] * c_cnorm[ncum(LB) + ib] *
-                   c_cnorm[ncum(LC) + ic];
-      }
-    }
+    eri3c_triplet<LC, LA, LB>(a, scr, gl, a.aux_list[lo], a.pairs[t - a.prefix[lo]], active);
     __syncwarp();
   }
+}
+
+// The paper's warp-specialised prescreening (Sec. 2.2.1, Algorithm 1), kept
+// as a measured variant: every warp screens batches of 32 consecutive
+// candidate triplets (aux shell of the window x pair of the class, pairs in
+// their original order), one per lane, and appends the survivors to a
+// 64-entry loop buffer in shared memory (warp ballot for the slots); as soon
+// as the buffer holds a warp's worth of work (32 / G triplets, G lanes per
+// triplet) the warp computes them together, and at the end the remainder.
+// head and tail are warp-uniform registers.  The buffer cannot overflow: it
+// holds fewer than 32 / G entries before a batch adds at most 32.
+template <int LC, int LA, int LB>
+__global__ void __launch_bounds__(256) k_eri3c_ring(Eri3cArgs a) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G, W = 32 / G;
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gl = lane % G, gw = lane / G;
+  const int groups_per_block = blockDim.x / G;
+  double *scr = smem + (size_t)(threadIdx.x / G) * O::SCR;
+  int64_t *ring = reinterpret_cast<int64_t *>(smem + (size_t)groups_per_block * O::SCR) + warp * 64;
+  const int64_t ncand = (int64_t)a.n_aux * a.np;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  int head = 0, tail = 0;
+  auto consume = [&](int cnt) {
+    const bool act = gw < cnt;
+    const int64_t c = ring[(head + (act ? gw : 0)) & 63];
+    eri3c_triplet<LC, LA, LB>(a, scr, gl, a.aux_list[c / a.np], a.pairs_orig[c % a.np], act);
+    __syncwarp();
+    head += cnt;
+  };
+  for (int64_t b0 = gwarp * 32; b0 < ncand; b0 += nwarps * 32) {
+    const int64_t c = b0 + lane;
+    bool keep = false;
+    if (c < ncand) keep = a.qaux[a.aux_list[c / a.np]] * a.qpair_orig[c % a.np] >= a.tau;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) ring[(tail + __popc(m & ((1u << lane) - 1u))) & 63] = c;
+    tail += __popc(m);
+    __syncwarp();
+    while (tail - head >= W) consume(W);
+  }
+  if (tail > head) consume(tail - head);
+}
+
+// The two-kernel alternative the paper argues against: a screening kernel
+// appends every surviving candidate to a global index list (capacity for
+// all candidates, since the count is unknown in advance), then a second
+// kernel computes the listed triplets.
+__global__ void __launch_bounds__(256) k_screen_list(Eri3cArgs a) {
+  const int64_t ncand = (int64_t)a.n_aux * a.np;
+  const int lane = threadIdx.x & 31;
+  for (int64_t b0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; b0 < ncand;
+       b0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = b0 + lane;
+    bool keep = false;
+    if (c < ncand) keep = a.qaux[a.aux_list[c / a.np]] * a.qpair_orig[c % a.np] >= a.tau;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    unsigned long long pos = 0;
+    if (lane == 0 && m) pos = atomicAdd(a.count, (unsigned long long)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (keep) a.list[pos + __popc(m & ((1u << lane) - 1u))] = c;
+  }
+}
+
+template <int LC, int LA, int LB>
+__global__ void __launch_bounds__(256) k_eri3c_list(Eri3cArgs a) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G;
+  const int group_in_block = threadIdx.x / G;
+  const int groups_per_block = blockDim.x / G;
+  double *scr = smem + (size_t)group_in_block * O::SCR;
+  const int64_t total = (int64_t)*a.count;
+  const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
+  const int warp_first_group = (threadIdx.x >> 5) * (32 / G);
+  const int64_t base0 = (int64_t)blockIdx.x * groups_per_block + warp_first_group;
+  for (int64_t base = base0; base < total; base += gstride) {
+    int64_t t = base + (group_in_block - warp_first_group);
+    const bool active = t < total;
+    if (!active) t = total - 1;
+    const int64_t c = a.list[t];
+    eri3c_triplet<LC, LA, LB>(a, scr, gl, a.aux_list[c / a.np], a.pairs_orig[c % a.np], active);
+    __syncwarp();
+  }
+}
+
+// variant 0: sorted prefix (k_eri3c), 1: loop buffer, 2: index list
+template <int LC, int LA, int LB>
+static int launch3v(const Eri3cArgs &a, int64_t total, int variant, cudaStream_t s) {
+  using O = Os<LA, LB, LC, 0>;
+  constexpr int G = O::G;
+  int groups = 256 / G;
+  while (groups > 32 / G && (size_t)groups * O::SCR * 8 + 8 * 64 * 8 > 196 * 1024)
+    groups -= 32 / G;
+  const size_t smem = (size_t)groups * O::SCR * 8 + (variant == 1 ? (size_t)(groups * G / 32) * 512 : 0);
+  if (smem > 227 * 1024) return BQC_E_UNSUPPORTED;
+  const int64_t cap = (int64_t)sm_count() * 16;
+  if (variant == 1) {
+    auto kern = k_eri3c_ring<LC, LA, LB>;
+    BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    const int64_t ncand = (int64_t)a.n_aux * a.np;
+    const int warps = groups * G / 32;
+    int64_t blocks = (ncand + 32 * warps - 1) / (32 * warps);
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, cap));
+    kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  } else {
+    auto kern = k_eri3c_list<LC, LA, LB>;
+    BQC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    const int64_t ncand = (int64_t)a.n_aux * a.np;
+    int64_t sb = std::max<int64_t>(1, std::min<int64_t>((ncand + 255) / 256, cap));
+    BQC_CUDA_TRY(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
+    k_screen_list<<<(unsigned)sb, 256, 0, s>>>(a);
+    BQC_LAUNCH_CHECK();
+    // the survivor count stays on the device: size the grid for all candidates
+    int64_t blocks = (ncand + groups - 1) / groups;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, cap));
+    kern<<<(unsigned)blocks, groups * G, smem, s>>>(a);
+  }
+  (void)total;
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
 }
 
 template <int LC, int LA, int LB>
@@ -617,10 +765,48 @@ static int dispatch3(int lc, int cls, const Eri3cArgs &a, int64_t total, cudaStr
   return BQC_E_UNSUPPORTED;
 }
 
+template <int LC>
+static int dispatch3v_pair(int cls, const Eri3cArgs &a, int64_t total, int v, cudaStream_t s) {
+  switch (cls) {
+    case 0: return launch3v<LC, 0, 0>(a, total, v, s);
+    case 1: return launch3v<LC, 1, 0>(a, total, v, s);
+    case 2: return launch3v<LC, 1, 1>(a, total, v, s);
+    case 3: return launch3v<LC, 2, 0>(a, total, v, s);
+    case 4: return launch3v<LC, 2, 1>(a, total, v, s);
+    case 5: return launch3v<LC, 2, 2>(a, total, v, s);
+  }
+  return BQC_E_UNSUPPORTED;
+}
+
+static int dispatch3v(int lc, int cls, const Eri3cArgs &a, int64_t total, int v, cudaStream_t s) {
+  switch (lc) {
+    case 0: return dispatch3v_pair<0>(cls, a, total, v, s);
+    case 1: return dispatch3v_pair<1>(cls, a, total, v, s);
+    case 2: return dispatch3v_pair<2>(cls, a, total, v, s);
+    case 3: return dispatch3v_pair<3>(cls, a, total, v, s);
+  }
+  return BQC_E_UNSUPPORTED;
+}
+
 int launch_eri3c(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *out, int64_t ld,
                  cudaStream_t s) {
-  if (p0 < 0 || p1 > b->naux || p0 > p1) return BQC_E_INVALID;
+  return launch_eri3c_variant(b, plan, p0, p1, out, ld, 0, s);
+}
+
+int launch_eri3c_variant(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *out,
+                         int64_t ld, int variant, cudaStream_t s) {
+  if (p0 < 0 || p1 > b->naux || p0 > p1 || variant < 0 || variant > 2) return BQC_E_INVALID;
   if (p0 == p1) return BQC_OK;
+  DBuf list, count;
+  if (variant == 2) {
+    int64_t maxc = 0;
+    for (int lc = 0; lc <= kMaxLAux; ++lc)
+      for (int cls = 0; cls < kNPairClass; ++cls)
+        maxc = std::max<int64_t>(maxc, (int64_t)(b->auxl_off[lc + 1] - b->auxl_off[lc]) *
+                                           (b->pair_off[cls + 1] - b->pair_off[cls]));
+    BQC_TRY(list.alloc(b->ctx, (size_t)std::max<int64_t>(1, maxc) * 8));
+    BQC_TRY(count.alloc(b->ctx, 8));
+  }
   for (int lc = 0; lc <= kMaxLAux; ++lc) {
     const int na = b->auxl_off[lc + 1] - b->auxl_off[lc];
     if (na == 0) continue;
@@ -661,9 +847,20 @@ int launch_eri3c(const Basis *b, const Eri3cPlan *plan, int p0, int p1, double *
       a.ld = ld;
       a.flag = b->ctx->flag;
       a.out_elems = (int64_t)(p1 - p0) * ld;
-      BQC_TRY(dispatch3(lc, cls, a, ntrip, s));
+      a.pairs_orig = b->d_pairs.as<int2>() + b->pair_off[cls];
+      a.qpair_orig = plan->d_qpair.as<double>() + b->pair_off[cls];
+      a.qaux = plan->d_qaux.as<double>();
+      a.tau = plan->tau;
+      a.np = np;
+      a.list = list.as<int64_t>();
+      a.count = count.as<unsigned long long>();
+      if (variant == 0)
+        BQC_TRY(dispatch3(lc, cls, a, ntrip, s));
+      else
+        BQC_TRY(dispatch3v(lc, cls, a, ntrip, variant, s));
     }
   }
+  if (variant == 2) BQC_CUDA_TRY(cudaStreamSynchronize(s));  // before the list is released
   return BQC_OK;
 }
 
@@ -1085,7 +1282,7 @@ int eri3c_plan(const Basis *b, double tau, const double *V_diag_dev, cudaStream_
   BQC_TRY(plan->d_pairs_sorted.alloc(ctx, np * sizeof(int2)));
   BQC_TRY(plan->d_qpair_sorted.alloc(ctx, np * sizeof(double)));
   BQC_TRY(plan->d_qaux.alloc(ctx, nas * sizeof(double)));
-  DBuf qpair, keys_tmp;
+  DBuf &qpair = plan->d_qpair;
   BQC_TRY(qpair.alloc(ctx, np * sizeof(double)));
   BQC_TRY(launch_schwarz_pairs(b, qpair.as<double>(), s));
   k_diag_sqrt_max<<<(nas + 127) / 128, 128, 0, s>>>(V_diag_dev, b->naux, b->aux.dev.fn,

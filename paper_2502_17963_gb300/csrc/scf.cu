@@ -532,6 +532,11 @@ extern "C" {
 int bqc_scf_run(bqc_ctx *ctx, bqc_df *df, const bqc_scf_opts *opts, bqc_stream_t stream,
                 bqc_scf_result *out) {
   if (!ctx || !df || !out) return BQC_E_INVALID;
+  if (df->is_shard()) {
+    set_error("bqc_scf_run needs the whole three-index tensor, not an aux shard", __FILE__,
+              __LINE__);
+    return BQC_E_INVALID;
+  }
   BQC_CUDA_TRY(cudaSetDevice(ctx->device));
   bqc_scf_opts o;
   o.diis_tol = 1e-8;

@@ -1246,7 +1246,7 @@ static int make_side_stream(Df *df, cudaStream_t s) {
 // largest row norm of B (for the per-build bound on |X|), read back once.
 static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   const Basis *b = df->basis;
-  const int n = b->nbf, naux = b->naux;
+  const int n = b->nbf, naux = df->naux_loc;
   const MixedPlan &m = ms->plan;
   Ctx *ctx = df->ctx;
   DBuf stat;
@@ -1324,7 +1324,7 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
 
 int mixed_setup(Df *df, int shadow, cudaStream_t s) {
   const Basis *b = df->basis;
-  const int n = b->nbf, naux = b->naux, no = b->nocc;
+  const int n = b->nbf, naux = df->naux_loc, no = b->nocc;
   MixedState *ms = new MixedState();
   df->mixed.reset(ms);
   ms->shadow = shadow;
@@ -1508,7 +1508,7 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   const int split = prec == BQC_PREC_MIXED_TF32 ? 1 : 3;
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
-  const int n = b->nbf, naux = b->naux;
+  const int n = b->nbf, naux = df->naux_loc;
   const int64_t rows = (int64_t)naux * n;
   const bool j64 = split == 3 && df->B64.p;
   BQC_TRY(mixed_xpass(df, C, kind, split, s, &ms->mapAh, &ms->mapAl, rows,
