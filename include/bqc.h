@@ -141,7 +141,11 @@ int bqc_int3c(const bqc_basis *basis, double schwarz, double *out_dev, bqc_strea
 
 /* ---------------------------------------------------------- DF tensor --- */
 
-typedef enum { BQC_DF_STORED = 0, BQC_DF_DIRECT = 1, BQC_DF_AUTO = 2 } bqc_df_mode;
+/* NONE: no density fitting; bqc_jk builds J and K directly from Schwarz-
+ * screened four-centre integrals (mu nu|lambda sigma), the conventional
+ * on-the-fly mean field the paper uses for molecules (Sec. 2.2.2), FP64 only;
+ * the auxiliary basis is ignored. */
+typedef enum { BQC_DF_STORED = 0, BQC_DF_DIRECT = 1, BQC_DF_AUTO = 2, BQC_DF_NONE = 3 } bqc_df_mode;
 
 /* Split shadows of B kept for the mixed precisions: NONE (FP64 builds only),
  * TF32 (full-square hi/lo TF32 parts: MIXED_TF32 and MIXED_TF32X3; 8 bytes
@@ -343,18 +347,19 @@ enum { BQC_SWITCH_NONE = 0, BQC_SWITCH_STAGE_TOL = 1, BQC_SWITCH_FLOOR = 2 };
  * bqc_jk.
  * Anchored incremental FP64 stage (opts.incremental = 1 with a mixed first
  * stage; no counterpart in the paper, the incremental Fock build of direct
- * SCF codes): F_k = F_(k-1) + 2 J[dD] - K[dD] with dD = D_k - D_(k-1)
- * factored as V+ V+^T - V- V-^T (eigenvectors of dD scaled by the square
- * roots of its positive and negative eigenvalues, at most nocc of each) and
- * J, K of V+ and V- built in the first stage's mixed precision, so the
- * rounding error of an increment scales with |dD|, not with |D|.  Full FP64
- * builds ("anchors") reset the accumulated error: at the switch, when the
- * DIIS error first falls below 100 x diis_tol, after 10 increments, and on
- * every iteration that would converge, so convergence (max|e| < diis_tol and
- * |dE| below the energy bar) is only ever declared on a full FP64 Fock
- * matrix and the reported energy is that build's.  After 8 anchors the
- * stage falls back to full builds.  History entries of incremental builds
- * carry the precision code -1.  With prec = MIXED_TF32 the first stage runs mixed and switches to
+ * SCF codes): F_k = F_a + 2 J[dD] - K[dD] with F_a the full FP64 Fock matrix
+ * of the last anchor build, dD = D_k - D_a factored as V+ V+^T - V- V-^T
+ * (eigenvectors of dD scaled by the square roots of its positive and
+ * negative eigenvalues, at most nocc of each) and J, K of V+ and V- built in
+ * the first stage's mixed precision, so the rounding error of F_k scales
+ * with |D_k - D_a|, not with |D|.  Anchors (full FP64 builds) are made at
+ * the switch, when the DIIS error first falls below 100 x diis_tol, after
+ * 10 increments, and on every iteration that would converge: an
+ * incremental iteration with max|e| < diis_tol and a stable energy is
+ * redone as a full FP64 build, which must confirm max|e| < diis_tol, so the
+ * reported energy and DIIS error are always those of a full FP64 Fock
+ * matrix.  After 8 anchors the stage falls back to full builds.  History
+ * entries of incremental builds carry the precision code -1.  With prec = MIXED_TF32 the first stage runs mixed and switches to
  * FP64 (DIIS subspace cleared) when the DIIS error drops below stage_tol, or
  * earlier once the mixed stage stops improving (its error floor, about
  * max|dF_mixed| / sqrt(smallest kept overlap eigenvalue), can lie above

@@ -28,7 +28,7 @@ PREC_MIXED_TF32X3 = 2
 PREC_MIXED_F16X3 = 3
 SHADOW_NONE, SHADOW_TF32, SHADOW_F16 = 0, 1, 2
 SERVE_BACKFILL, SERVE_FIFO = 0, 1
-DF_STORED, DF_DIRECT, DF_AUTO = 0, 1, 2
+DF_STORED, DF_DIRECT, DF_AUTO, DF_NONE = 0, 1, 2, 3
 
 
 class BqcError(RuntimeError):

@@ -223,7 +223,7 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
     }
     mode = df_stored_bytes(n, naux, no, o.keep_fp32) <= limit ? BQC_DF_STORED : BQC_DF_DIRECT;
   }
-  if (mode != BQC_DF_STORED && mode != BQC_DF_DIRECT) return BQC_E_INVALID;
+  if (mode != BQC_DF_STORED && mode != BQC_DF_DIRECT && mode != BQC_DF_NONE) return BQC_E_INVALID;
   if (o.keep_fp32 < BQC_SHADOW_NONE || o.keep_fp32 > BQC_SHADOW_F16) return BQC_E_INVALID;
   // aux shard [P0, P1) (stored mode): both 0 selects every aux function
   int P0 = o.aux_begin, P1 = o.aux_end;
@@ -233,11 +233,12 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
     return BQC_E_INVALID;
   }
   const bool shard = P0 != 0 || P1 != naux;
+  if (shard && mode == BQC_DF_NONE) return BQC_E_INVALID;
   if (shard && mode != BQC_DF_STORED) {
     set_error("bqc_df_build: aux shards are a stored-mode feature", __FILE__, __LINE__);
     return BQC_E_UNSUPPORTED;
   }
-  if (o.schwarz < 0.0) o.schwarz = (mode == BQC_DF_STORED) ? 1e-12 : 1e-10;
+  if (o.schwarz < 0.0) o.schwarz = (mode == BQC_DF_DIRECT) ? 1e-10 : 1e-12;
   if (o.aux_block <= 0) o.aux_block = 1024;
   bqc_df *df = new (std::nothrow) bqc_df();
   if (!df) return BQC_E_OOM;
@@ -254,6 +255,12 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
     return st;
   };
   int st;
+  if (mode == BQC_DF_NONE) {  // conventional four-centre J/K: no auxiliary tensor
+    if ((st = jk4c_setup(df, s)) != BQC_OK) return fail(st);
+    if ((st = ctx->check_flag(s)) != BQC_OK) return fail(st);
+    *out = df;
+    return BQC_OK;
+  }
   // metric and its Cholesky factor
   if ((st = df->L.alloc(ctx, (size_t)naux * naux * 8)) != BQC_OK) return fail(st);
   if ((st = launch_int2c(basis, df->L.as<double>(), s)) != BQC_OK) return fail(st);
@@ -354,6 +361,7 @@ int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
     BQC_CUDA_TRY(cudaMemcpyAsync(out, df->B64.p, (size_t)df->naux_loc * df->npair * 8,
                                  cudaMemcpyDeviceToDevice, s));
   } else if (which == 1) {
+    if (!df->L.p) return BQC_E_INVALID;
     BQC_CUDA_TRY(
         cudaMemcpyAsync(out, df->L.p, (size_t)naux * naux * 8, cudaMemcpyDeviceToDevice, s));
   } else {
@@ -364,7 +372,8 @@ int bqc_df_copy(const bqc_df *df, int which, double *out, bqc_stream_t stream) {
 
 int bqc_int3c_screened(const bqc_df *df, int p0, int p1, int variant, double *out,
                        bqc_stream_t stream) {
-  if (!df || !out || variant < 0 || variant > 2) return BQC_E_INVALID;
+  if (!df || !out || variant < 0 || variant > 2 || df->mode == BQC_DF_NONE)
+    return BQC_E_INVALID;
   if (p0 < 0 || p1 > df->basis->naux || p0 >= p1) return BQC_E_INVALID;
   BQC_CUDA_TRY(cudaSetDevice(df->ctx->device));
   return launch_eri3c_variant(df->basis, &df->plan, p0, p1, out, df->npair, variant,
@@ -409,6 +418,7 @@ int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K
   if (df->timing) df->timed = true;
   df->last_mixed = prec != BQC_PREC_FP64;
   if (df->mode == BQC_DF_DIRECT) return jk_direct(df, C, prec, J, K, s);
+  if (df->mode == BQC_DF_NONE) return jk_4c(df, C, prec, J, K, s);
   if (prec == BQC_PREC_FP64) return jk_fp64_stored(df, C, J, K, s);
   if (prec == BQC_PREC_MIXED_TF32 || prec == BQC_PREC_MIXED_TF32X3 ||
       prec == BQC_PREC_MIXED_F16X3) {

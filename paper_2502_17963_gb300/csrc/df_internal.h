@@ -15,6 +15,10 @@ struct DirectMixed;
 struct DirectMixedDeleter {
   void operator()(DirectMixed *p) const;
 };
+struct Jk4Plan;
+struct Jk4Deleter {
+  void operator()(Jk4Plan *p) const;
+};
 
 struct Df {
   Ctx *ctx = nullptr;
@@ -50,6 +54,8 @@ struct Df {
   DBuf Kpart64;
   int aux_block = 1024;
   std::unique_ptr<DirectMixed, DirectMixedDeleter> dmixed;  // tensor-core state
+  // conventional four-centre mode (no density fitting)
+  std::unique_ptr<Jk4Plan, Jk4Deleter> jk4;
   // phase timing (bqc_df_timing)
   bool timing = false, timed = false, last_mixed = false;
   int j_from = 2;  // event that opens the J phase of the last mixed stored build
@@ -93,6 +99,8 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
 int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s);
 int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 size_t df_stored_bytes(int n, int naux, int nocc, int shadow);
+int jk4c_setup(Df *df, cudaStream_t s);
+int jk_4c(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 
 }  // namespace bqc
 

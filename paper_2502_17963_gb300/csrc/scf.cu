@@ -263,6 +263,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   }
   bool need_anchor = true;    // the first FP64-stage build is full
   bool last_incremental = false;
+  bool confirming = false;     // a full build redoing a converged incremental iteration
   int anchors = 0, inc_since_anchor = 0;
   double anchor_err = INFINITY;
   std::vector<double> hev;
@@ -272,7 +273,9 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   // threads, e.g. other serving slots, keep launching meanwhile).
   GraphSet graphs;
   cudaGraphExec_t *gexec = graphs.g;
-  // F = Facc + G[D_k - Dref] in the mixed precision (no graph: the
+  // F = Facc + G[D_k - Dref] in the mixed precision, relative to the last
+  // anchor (Facc, Dref = its full FP64 Fock matrix and density), so the
+  // errors of successive increments do not accumulate (no graph: the
   // eigen-decomposition reads its status on the host).
   auto incremental_build = [&]() -> int {
     BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, no, &one, Cc.as<double>(), n,
@@ -306,8 +309,6 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     k_inc_fock<<<nblk(nn), 256, 0, s>>>(nn, Facc.as<double>(), J.as<double>(), J2.as<double>(),
                                         K.as<double>(), K2.as<double>(), F.as<double>());
     BQC_LAUNCH_CHECK();
-    BQC_CUDA_TRY(cudaMemcpyAsync(Facc.p, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
-    BQC_CUDA_TRY(cudaMemcpyAsync(Dref.p, Dk.p, nn * 8, cudaMemcpyDeviceToDevice, s));
     return BQC_OK;
   };
   auto fock_build = [&](int prec) -> int {
@@ -404,18 +405,22 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
       h[1] = emax;
       h[2] = E;
     }
-    if (stage == BQC_PREC_FP64 && emax < o.diis_tol && have_prev &&
-        std::fabs(E - Eprev) < std::max(o.energy_tol, DBL_EPSILON * n * std::fabs(E))) {
+    const bool e_stable =
+        have_prev && std::fabs(E - Eprev) < std::max(o.energy_tol, DBL_EPSILON * n * std::fabs(E));
+    if (stage == BQC_PREC_FP64 && emax < o.diis_tol && (e_stable || confirming)) {
       if (!last_incremental) {
         converged = true;
         break;
       }
-      // converged on an incremental Fock matrix: redo the iteration as a
-      // full FP64 build and test again
+      // converged on an incremental Fock matrix (energy stable within the
+      // increments of one anchor, which share their rounding): redo the
+      // iteration as a full FP64 build, which must confirm the DIIS error
       need_anchor = true;
+      confirming = true;
       --it;
       continue;
     }
+    confirming = false;
     if (inc_stage) {
       if (!last_incremental) {
         ++anchors;
