@@ -352,7 +352,9 @@ enum { BQC_SWITCH_NONE = 0, BQC_SWITCH_STAGE_TOL = 1, BQC_SWITCH_FLOOR = 2 };
  * (eigenvectors of dD scaled by the square roots of its positive and
  * negative eigenvalues, at most nocc of each) and J, K of V+ and V- built in
  * the first stage's mixed precision, so the rounding error of F_k scales
- * with |D_k - D_a|, not with |D|.  Anchors (full FP64 builds) are made at
+ * with |D_k - D_a|, not with |D|; in stored mode the Coulomb part J[dD] is
+ * instead formed in FP64 from dD itself (two streaming passes over the FP64
+ * B), which avoids the cancellation between the J of V+ and of V-.  Anchors (full FP64 builds) are made at
  * the switch, when the DIIS error first falls below 100 x diis_tol, after
  * 10 increments, and on every iteration that would converge: an
  * incremental iteration with max|e| < diis_tol and a stable energy is

@@ -87,6 +87,59 @@ __global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
   }
 }
 
+// J pass over a packed FP32 copy of B (the split-FP16 build): rows of ld4
+// floats (Npair rounded up to 4, zero padded); each thread owns four
+// adjacent columns (one 16-byte load per P, eight in flight), multiplies and
+// sums in FP32 over runs of 32 P and adds the runs in FP64.  Half the bytes
+// of the FP64 pass and no FP64 arithmetic: the pass is bound by memory
+// parallelism, which beside the SYRK is what a J block gets.
+__global__ void __launch_bounds__(256) k_jpass32(const float *__restrict__ B,
+                                                 const float *__restrict__ w, int P0, int P1,
+                                                 int64_t ld4, int y0, double *__restrict__ Jp) {
+  const int64_t c4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (c4 >= ld4) return;
+  const int per = (P1 - P0 + gridDim.y - 1) / gridDim.y;
+  const int Pa = P0 + blockIdx.y * per, Pb = min(P1, Pa + per);
+  const float4 *b4 = reinterpret_cast<const float4 *>(B + c4);
+  const int64_t st = ld4 / 4;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int P = Pa;
+  while (P < Pb) {
+    const int P1 = min(Pb, P + 32);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (; P + 8 <= P1; P += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(b4 + (int64_t)(P + k) * st);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float wp = __ldg(w + P + k);
+        s0 = fmaf(wp, v[k].x, s0);
+        s1 = fmaf(wp, v[k].y, s1);
+        s2 = fmaf(wp, v[k].z, s2);
+        s3 = fmaf(wp, v[k].w, s3);
+      }
+    }
+    for (; P < P1; ++P) {
+      const float4 v = __ldg(b4 + (int64_t)P * st);
+      const float wp = __ldg(w + P);
+      s0 = fmaf(wp, v.x, s0);
+      s1 = fmaf(wp, v.y, s1);
+      s2 = fmaf(wp, v.z, s2);
+      s3 = fmaf(wp, v.w, s3);
+    }
+    a0 += s0;
+    a1 += s1;
+    a2 += s2;
+    a3 += s3;
+  }
+  double *out = Jp + (int64_t)(y0 + blockIdx.y) * ld4 + c4;
+  out[0] = a0;
+  out[1] = a1;
+  out[2] = a2;
+  out[3] = a3;
+}
+
 // J[r][c] = sum_y Jp[y][pair(r, c)] (full symmetric N x N, chunks in order).
 __global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n, double *J) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,6 +182,74 @@ int jpass_fp64(Df *df, double *J, cudaStream_t s) {
                                                                          npair, n, J);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
+}
+
+int64_t jpass32_ld(int64_t npair) { return (npair + 3) / 4 * 4; }
+
+// Packed lower triangle of a symmetric N x N matrix with the off-diagonal
+// doubled: D2[mu(mu+1)/2 + nu] = (2 - delta_mu nu) D[mu][nu] (so that
+// B_P : D = sum over the packed entries of B_P D2).
+__global__ void k_pack_sym2(const double *__restrict__ D, int n, double *__restrict__ D2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * (n + 1) / 2) return;
+  int mu = (int)((sqrt(8.0 * (double)i + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(mu + 1) * (mu + 2) / 2 <= i) ++mu;
+  while ((int64_t)mu * (mu + 1) / 2 > i) --mu;
+  const int nu = (int)(i - (int64_t)mu * (mu + 1) / 2);
+  D2[i] = (mu == nu ? 1.0 : 2.0) * D[(int64_t)mu * n + nu];
+}
+
+// w[P] = sum_c B[P][c] D2[c] over the packed FP64 B (one block per P).
+__global__ void __launch_bounds__(256) k_bdot(const double *__restrict__ B, int64_t npair,
+                                              const double *__restrict__ D2, double *w) {
+  const double *b = B + (int64_t)blockIdx.x * npair;
+  double s = 0.0;
+  for (int64_t c = threadIdx.x; c < npair; c += blockDim.x) s = fma(b[c], D2[c], s);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w[blockIdx.x] = red[0];
+}
+
+int jfp64_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s) {
+  if (df->mode != BQC_DF_STORED || !df->B64.p) return BQC_E_INVALID;
+  const int n = df->basis->nbf;
+  k_pack_sym2<<<(unsigned)((df->npair + 255) / 256), 256, 0, s>>>(D, n, D2);
+  BQC_LAUNCH_CHECK();
+  k_bdot<<<(unsigned)df->naux_loc, 256, 0, s>>>(df->B64.as<double>(), df->npair, D2,
+                                                df->w.as<double>());
+  BQC_LAUNCH_CHECK();
+  return jpass_fp64(df, J, s);
+}
+
+int jpass_fp32_range(Df *df, const float *B32p, const float *w32, int P0, int P1, int y0,
+                     cudaStream_t s) {
+  const int64_t ld4 = jpass32_ld(df->npair);
+  const int sp = jpass_split(ld4, P1 - P0);
+  if (df->Jp.n < (size_t)(y0 + sp) * ld4 * 8) return BQC_E_INVALID;
+  k_jpass32<<<dim3((unsigned)((ld4 / 4 + 255) / 256), (unsigned)sp), 256, 0, s>>>(
+      B32p, w32, P0, P1, ld4, y0, df->Jp.as<double>());
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int jpass_fp32_unpack(Df *df, int nslice, double *J, cudaStream_t s) {
+  const int n = df->basis->nbf;
+  // the chunk partials have row stride ld4 >= npair: sum them with that stride
+  k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(
+      df->Jp.as<double>(), nslice, jpass32_ld(df->npair), n, J);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int jpass_fp32(Df *df, const float *B32p, const float *w32, double *J, cudaStream_t s) {
+  const int naux = df->naux_loc;
+  BQC_TRY(jpass_fp32_range(df, B32p, w32, 0, naux, 0, s));
+  return jpass_fp32_unpack(df, jpass_split(jpass32_ld(df->npair), naux), J, s);
 }
 
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {

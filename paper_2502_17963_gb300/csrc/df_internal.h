@@ -59,17 +59,22 @@ struct Df {
   // phase timing (bqc_df_timing)
   bool timing = false, timed = false, last_mixed = false;
   int j_from = 2;  // event that opens the J phase of the last mixed stored build
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void mark(int i, cudaStream_t s) {
     if (timing && ev[i]) cudaEventRecord(ev[i], s);
   }
   // side stream of the mixed build: J runs there concurrently with the tensor-core passes
   cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t tcs = nullptr;  // tensor-core stream, one priority level above side
+  cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, prep = nullptr, tjoin = nullptr;
   ~Df() {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
+    if (fork2) cudaEventDestroy(fork2);
+    if (prep) cudaEventDestroy(prep);
+    if (tjoin) cudaEventDestroy(tjoin);
+    if (tcs) cudaStreamDestroy(tcs);
     if (join) cudaEventDestroy(join);
     if (side) cudaStreamDestroy(side);
   }
@@ -91,6 +96,18 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 // J = sum_P w_P B_P from the packed FP64 B and df->w (FP64), full symmetric.
 int jpass_fp64(Df *df, double *J, cudaStream_t s);
+// J = sum_P w32_P B32p_P over a packed FP32 copy of B (rows of jpass32_ld(Npair)).
+int64_t jpass32_ld(int64_t npair);
+int jpass_fp32(Df *df, const float *B32p, const float *w32, double *J, cudaStream_t s);
+// The same in pieces: partials of aux functions [P0, P1) into partial slices
+// starting at y0, then the sum of nslice slices into J.
+int jpass_fp32_range(Df *df, const float *B32p, const float *w32, int P0, int P1, int y0,
+                     cudaStream_t s);
+int jpass_fp32_unpack(Df *df, int nslice, double *J, cudaStream_t s);
+int jpass_split(int64_t npair, int naux);
+// J[D] = sum_P (B_P : D) B_P in FP64 over the stored FP64 B for a symmetric
+// N x N matrix D (any sign), D2 an Npair scratch.
+int jfp64_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s);
 int direct_setup(Df *df, cudaStream_t s);
 size_t direct_mixed_bytes(int n, int naux, int nocc, int bs);
 int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s);

@@ -254,10 +254,11 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   // anchored incremental FP64 stage (see bqc.h): state
   const bool inc_on = o.incremental != 0 && o.prec != BQC_PREC_FP64;
   const int mixed_prec = o.prec;
-  DBuf Facc, Dref, Dk, Vp, Vm, J2, K2, evd;
+  DBuf Facc, Dref, Dk, Vp, Vm, J2, K2, evd, Jx, D2p;
   if (inc_on) {
-    for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2}) BQC_TRY(p->alloc(ctx, nn * 8));
+    for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2, &Jx}) BQC_TRY(p->alloc(ctx, nn * 8));
     BQC_TRY(evd.alloc(ctx, (size_t)n * 8));
+    BQC_TRY(D2p.alloc(ctx, (size_t)n * (n + 1) / 2 * 8));
     BQC_TRY(Vp.alloc(ctx, (size_t)n * no * 8));
     BQC_TRY(Vm.alloc(ctx, (size_t)n * no * 8));
   }
@@ -283,6 +284,11 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     const double mone = -1.0;
     BQC_BLAS_TRY(cublasDgeam(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, &one, Dk.as<double>(), n,
                              &mone, Dref.as<double>(), n, t1.as<double>(), n));
+    // the Coulomb part of the increment in FP64 straight from dD (stored
+    // mode): J is linear in the density, so no factorisation and no
+    // cancellation between the two signed parts
+    const bool jexact = df->mode == BQC_DF_STORED && df->B64.p;
+    if (jexact) BQC_TRY(jfp64_of_density(df, t1.as<double>(), D2p.as<double>(), Jx.as<double>(), s));
     BQC_TRY(eigh(w, ctx, t1.as<double>(), n, evd.as<double>(), work, info, s));
     hev.resize(n);
     BQC_CUDA_TRY(cudaMemcpyAsync(hev.data(), evd.p, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -306,6 +312,10 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
                    K.as<double>(), (bqc_stream_t)s));
     BQC_TRY(bqc_jk(static_cast<bqc_df *>(df), Vm.as<double>(), no, mixed_prec, J2.as<double>(),
                    K2.as<double>(), (bqc_stream_t)s));
+    if (jexact) {  // J[dD] exact: J+ - J- replaced by Jx
+      BQC_CUDA_TRY(cudaMemcpyAsync(J.p, Jx.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+      BQC_CUDA_TRY(cudaMemsetAsync(J2.p, 0, nn * 8, s));
+    }
     k_inc_fock<<<nblk(nn), 256, 0, s>>>(nn, Facc.as<double>(), J.as<double>(), J2.as<double>(),
                                         K.as<double>(), K2.as<double>(), F.as<double>());
     BQC_LAUNCH_CHECK();

@@ -147,7 +147,9 @@ struct MixScale {
 };
 
 struct XpassParams {
-  int64_t rows;      // Naux * N  (M of the GEMM)
+  int64_t rows;      // rows of this launch (M of the GEMM), starting at row0
+  int64_t row0;      // first row (a launch may cover a range of aux functions)
+  int64_t wstride;   // row stride of the w partials (all rows of the tensor)
   int n;             // N (rows per aux function)
   int ldx;           // row length of X and Cf
   int ncg;           // column groups (tile columns = XN each)
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int64_t kg = 0;  // k-blocks issued by this CTA
       for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
-        const int64_t m0 = (t / p.ncg) * kBM;
+        const int64_t m0 = p.row0 + (t / p.ncg) * kBM;
         const int c0 = (int)(t % p.ncg) * XN;
         for (int kb = 0; kb < p.kblocks && ok; ++kb, ++kg) {
           const int s = (int)(kg % p.stages);
@@ -287,8 +289,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3, h = (warp - 2) >> 2;
     int64_t g = 0;
     for (int64_t t = blockIdx.x; t < p.tiles; t += gridDim.x) {
-      const int64_t m0 = (t / p.ncg) * kBM;
+      const int64_t m0 = p.row0 + (t / p.ncg) * kBM;
       const int cg = (int)(t % p.ncg);
+      const int64_t row_end = p.row0 + p.rows;
       float acc[HALF];
 #pragma unroll
       for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
       const int64_t row = m0 + q * 32 + lane;
-      if (KIND == kKindF16 && ok && row < p.rows) {
+      if (KIND == kKindF16 && ok && row < row_end) {
         // scaled X split into FP16 hi + lo (each rounded to nearest), and the
         // fused w partial sum_i X[row][i] C[mu][i] of the unscaled X
         const float xo = p.scale->x_out, xu = p.scale->x_unscale;
@@ -342,9 +345,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<uint4 *>(xh + c) = *reinterpret_cast<const uint4 *>(hv);
           *reinterpret_cast<uint4 *>(xl + c) = *reinterpret_cast<const uint4 *>(lv);
         }
-        p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum * xu;
+        p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum * xu;
       }
-      if (KIND == kKindTF32 && EPI == 0 && ok && row < p.rows) {
+      if (KIND == kKindTF32 && EPI == 0 && ok && row < row_end) {
         const int mu = (int)(row % p.n);
         const int col = cg * XN + h * HALF;
         float *xh = p.Xh + row * p.ldx + col;
@@ -372,9 +375,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<float4 *>(xl + c) = lv;
           }
         }
-        p.wpart[(int64_t)(2 * cg + h) * p.rows + row] = wsum;
+        p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum;
       }
-      if (KIND == kKindTF32 && EPI == 1 && ok && row < p.rows && (int)(row % p.bk) < p.bkv) {
+      if (KIND == kKindTF32 && EPI == 1 && ok && row < row_end && (int)(row % p.bk) < p.bkv) {
         // consecutive lanes hold consecutive q of one mu: coalesced per column
         const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
         const int col = cg * XN + h * HALF;
@@ -396,8 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // w[P] = sum over partials and mu of wpart[k][P*N + mu] (FP64); also fp32 w.
 __global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t rows, int nparts,
-                                                 int n, double *w, float *w32) {
-  const int P = blockIdx.x;
+                                                 int n, double *w, float *w32, int P0) {
+  const int P = P0 + blockIdx.x;
   double s = 0.0;
   for (int g = 0; g < nparts; ++g)
     for (int m = threadIdx.x; m < n; m += blockDim.x) s += wpart[g * rows + (int64_t)P * n + m];
@@ -989,6 +992,16 @@ __global__ void k_expand_split16(const double *__restrict__ B, int n, int ld, in
   Bl[i] = __float2half_rn(l);
 }
 
+// Packed FP32 copy of B for the J pass of the split-FP16 build: rows of ld4
+// floats (Npair rounded up to 4), zero padded.
+__global__ void k_pack_f32(const double *__restrict__ B, int64_t npair, int64_t ld4, int np,
+                           float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)np * ld4) return;
+  const int64_t P = i / ld4, c = i % ld4;
+  out[i] = c < npair ? (float)B[P * npair + c] : 0.0f;
+}
+
 // *out = max over rows of sum_c Bh[row][c]^2 (one warp per row; float bits).
 __global__ void __launch_bounds__(256) k_rowsq_max16(const __half *__restrict__ Bh, int64_t rows,
                                                      int ld, unsigned *out) {
@@ -1155,6 +1168,7 @@ size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow) {
     b += (size_t)2 * naux * n * m.ldx * 2;                           // Xh16, Xl16
     b += (size_t)2 * m.ldx * m.ld16 * 2 + (size_t)n * m.ldx * 4;     // C split, Cf
     b += (size_t)(nocc + 1) * 4 + 256;                               // statistics, scales
+    b += (size_t)naux * jpass32_ld((int64_t)n * (n + 1) / 2) * 4;   // packed FP32 B (J pass)
   } else {
     b += (size_t)2 * naux * n * m.ld * 4;                            // Bh, Bl
     b += (size_t)2 * naux * n * m.ldx * 4;                           // Xh, Xl
@@ -1170,11 +1184,12 @@ struct MixedState {
   DBuf Bl, Xl, Cl, Cf, wpart, w32;
   // FP16 split
   DBuf Bh16, Bl16, Xh16, Xl16, Ch16, Cl16, cstat, scale;
+  DBuf B32p;             // packed FP32 copy of B for the J pass
   int eB = 0;            // s_B = 2^eB
   double rownorm = 0.0;  // max_{P,mu} ||B_P,mu .||_2, unscaled, with a safety factor
   size_t bytes() const {
     return Bl.n + Xl.n + Cl.n + Cf.n + wpart.n + w32.n + Bh16.n + Bl16.n + Xh16.n + Xl16.n +
-           Ch16.n + Cl16.n + cstat.n + scale.n;
+           Ch16.n + Cl16.n + cstat.n + scale.n + B32p.n;
   }
 };
 
@@ -1230,15 +1245,25 @@ static int dispatch_xn(int xn, int kind, int split, int epi, size_t smem, const 
 
 static int make_side_stream(Df *df, cudaStream_t s) {
   if (df->side) return BQC_OK;
-  // the side stream inherits the caller's priority (serving ranks requests by it)
-  int prio = 0;
+  // the side stream (J) inherits the caller's priority (serving ranks
+  // requests by it); the tensor-core stream runs one level above it, so that
+  // the block scheduler starts a persistent tensor-core kernel's CTAs before
+  // pending J blocks (otherwise J blocks fill every SM first and the two
+  // passes serialise)
+  int prio = 0, least = 0, greatest = 0;
   if (s && cudaStreamGetPriority(s, &prio) != cudaSuccess) {
     cudaGetLastError();
     prio = 0;
   }
+  BQC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   BQC_CUDA_TRY(cudaStreamCreateWithPriority(&df->side, cudaStreamNonBlocking, prio));
+  BQC_CUDA_TRY(cudaStreamCreateWithPriority(&df->tcs, cudaStreamNonBlocking,
+                                            std::max(greatest, prio - 1)));
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork, cudaEventDisableTiming));
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
+  BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork2, cudaEventDisableTiming));
+  BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->prep, cudaEventDisableTiming));
+  BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->tjoin, cudaEventDisableTiming));
   return BQC_OK;
 }
 
@@ -1287,6 +1312,19 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   std::memcpy(&maxsq, &hb, 4);
   // |B row| <= |Bh row| / (1 - 2^-11); the factor also covers the float sums
   ms->rownorm = std::sqrt((double)maxsq) / (double)sB * (1.0 + 1.0 / 256.0);
+  {  // packed FP32 B for the J pass, and room for its chunk partials
+    const int64_t ld4 = jpass32_ld(df->npair);
+    BQC_TRY(ms->B32p.alloc(ctx, (size_t)naux * ld4 * 4));
+    const int64_t tot = (int64_t)naux * ld4;
+    k_pack_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(df->B64.as<double>(), df->npair, ld4,
+                                                             naux, ms->B32p.as<float>());
+    BQC_LAUNCH_CHECK();
+    const int ph = naux / 2;
+    const size_t need = (size_t)std::max(jpass_split(ld4, naux),
+                                         jpass_split(ld4, std::max(1, ph)) +
+                                             jpass_split(ld4, naux - ph)) * ld4 * 8;
+    if (df->Jp.n < need) BQC_TRY(df->Jp.alloc(ctx, need));
+  }
   BQC_TRY(ms->Xh16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
   BQC_TRY(ms->Xl16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
   BQC_TRY(ms->Ch16.alloc(ctx, (size_t)m.ldx * m.ld16 * 2));
@@ -1391,13 +1429,16 @@ int mixed_setup(Df *df, int shadow, cudaStream_t s) {
 // contraction w.
 static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_t s,
                        const CUtensorMap *Ah, const CUtensorMap *Al, int64_t rows, float *Xh,
-                       float *Xl, double *w_out) {
+                       float *Xl, double *w_out, int P0 = 0, int P1 = -1, bool prep = true) {
+  // rows: all rows of the A operands; the launch covers aux functions [P0, P1)
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, no = b->nocc;
-  df->mark(0, s);
-  if (kind == kKindF16) {
+  if (P1 < 0) P1 = (int)(rows / n);
+  if (prep && P1 > P0) df->mark(0, s);
+  if (!prep) {
+  } else if (kind == kKindF16) {
     const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld16, (int64_t)n * m.ldx);
     BQC_CUDA_TRY(cudaMemsetAsync(ms->cstat.p, 0, ms->cstat.n, s));
     k_cstats<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(C, n, no, ms->cstat.as<float>());
@@ -1416,9 +1457,12 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
         ms->Cf.as<float>());
     BQC_LAUNCH_CHECK();
   }
-  df->mark(1, s);
+  if (prep) df->mark(1, s);
+  if (P1 <= P0) return BQC_OK;
   XpassParams p;
-  p.rows = rows;
+  p.row0 = (int64_t)P0 * n;
+  p.rows = (int64_t)(P1 - P0) * n;
+  p.wstride = rows;
   p.n = n;
   p.ldx = m.ldx;
   p.ncg = m.ncg;
@@ -1426,7 +1470,7 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
   p.kblocks = ((kind == kKindF16 ? m.ld16 : m.ld) + ke - 1) / ke;
   const int k = split == 3 ? 1 : 0;
   p.stages = m.xp_stages[k];
-  p.tiles = (rows + kBM - 1) / kBM * m.ncg;
+  p.tiles = (p.rows + kBM - 1) / kBM * m.ncg;
   p.Xh = Xh;
   p.Xl = Xl;
   p.Xh16 = kind == kKindF16 ? ms->Xh16.as<__half>() : nullptr;
@@ -1443,8 +1487,8 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
   BQC_TRY(dispatch_xn(m.xn, kind, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl,
                       grid, s));
   if (w_out) {
-    k_wreduce<<<(unsigned)(rows / n), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
-                                                    w_out, ms->w32.as<float>());
+    k_wreduce<<<(unsigned)(P1 - P0), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
+                                                   w_out, ms->w32.as<float>(), P0);
     BQC_LAUNCH_CHECK();
   }
   return BQC_OK;
@@ -1489,12 +1533,14 @@ static int mixed_syrk(Df *df, int kind, int split, const CUtensorMap *Xh, const 
 
 // w comes fused from the X pass in every mixed precision (FP32 row partials
 // of X C, summed in FP64).  The J pass then runs on the side stream,
-// concurrently with the SYRK: 3xTF32 and FP16x3 read the packed FP64 B
-// (FP64 FMAs), single-pass TF32 reads the TF32 shadow.  Reading B in FP64
-// matters: with the split of B in the J pass, max|dJ| is only ~1e-6, but in a
-// diffuse basis the orthogonalisation amplifies it (by up to 1/sqrt(s_min))
-// into a DIIS error of ~1e-4, which would set the mixed SCF's error floor;
-// the error of the fused w, a smooth Coulomb-like perturbation, stays ~1e-7.
+// concurrently with the SYRK: 3xTF32 reads the packed FP64 B (FP64 FMAs),
+// FP16x3 a packed FP32 copy of B (FP32 FMAs, half the bytes), single-pass
+// TF32 the TF32 shadow.  The precision of B in the J pass matters: with the
+// 22-bit split of B there, max|dJ| is only ~1e-6, but in a diffuse basis the
+// orthogonalisation amplifies it (by up to 1/sqrt(s_min)) into a DIIS error
+// of ~1e-4, which would set the mixed SCF's error floor; FP32 (24 bits, 4x
+// finer) keeps J's share of that floor below K's.  The error of the fused
+// w, a smooth Coulomb-like perturbation, stays ~1e-7.
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   if (!ms) return BQC_E_INVALID;
@@ -1510,7 +1556,43 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   const Basis *b = df->basis;
   const int n = b->nbf, naux = df->naux_loc;
   const int64_t rows = (int64_t)naux * n;
-  const bool j64 = split == 3 && df->B64.p;
+  const bool j64 = split == 3 && df->B64.p && kind == kKindTF32;
+  if (kind == kKindF16 && df->side && df->tcs && naux >= 2) {
+    // Two halves of the aux index on the tensor-core stream: X pass (h1),
+    // X pass (h2), SYRK, back to back; the J pass of each half follows it on
+    // the side stream, beside the next tensor-core kernel.
+    const int Ph = naux / 2;
+    cudaStream_t ts = df->tcs, js = df->side;
+    df->mark(0, s);
+    BQC_TRY(mixed_xpass(df, C, kind, split, s, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                        nullptr, 0, 0, true));  // C split and scales only (no rows)
+    BQC_CUDA_TRY(cudaEventRecord(df->prep, s));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(ts, df->prep, 0));
+    BQC_TRY(mixed_xpass(df, C, kind, split, ts, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                        df->w.as<double>(), 0, Ph, false));
+    if (df->timing && df->ev[6]) cudaEventRecord(df->ev[6], ts);
+    df->j_from = 6;
+    BQC_CUDA_TRY(cudaEventRecord(df->fork, ts));
+    BQC_TRY(mixed_xpass(df, C, kind, split, ts, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                        df->w.as<double>(), Ph, naux, false));
+    if (df->timing && df->ev[2]) cudaEventRecord(df->ev[2], ts);
+    BQC_CUDA_TRY(cudaEventRecord(df->fork2, ts));
+    BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, ts));
+    if (df->timing && df->ev[3]) cudaEventRecord(df->ev[3], ts);
+    BQC_CUDA_TRY(cudaEventRecord(df->tjoin, ts));
+    const int sp1 = jpass_split(jpass32_ld(df->npair), Ph);
+    BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork, 0));
+    BQC_TRY(jpass_fp32_range(df, ms->B32p.as<float>(), ms->w32.as<float>(), 0, Ph, 0, js));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork2, 0));
+    BQC_TRY(jpass_fp32_range(df, ms->B32p.as<float>(), ms->w32.as<float>(), Ph, naux, sp1, js));
+    BQC_TRY(jpass_fp32_unpack(df, sp1 + jpass_split(jpass32_ld(df->npair), naux - Ph), J, js));
+    if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
+    BQC_CUDA_TRY(cudaEventRecord(df->join, js));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->tjoin, 0));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->join, 0));
+    df->mark(4, s);
+    return BQC_OK;
+  }
   BQC_TRY(mixed_xpass(df, C, kind, split, s, &ms->mapAh, &ms->mapAl, rows,
                       kind == kKindF16 ? nullptr : df->X32.as<float>(),
                       kind == kKindF16 ? nullptr : ms->Xl.as<float>(), df->w.as<double>()));
@@ -1522,7 +1604,9 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     BQC_CUDA_TRY(cudaStreamWaitEvent(df->side, df->fork, 0));
     js = df->side;
   }
-  if (j64) {
+  if (kind == kKindF16) {
+    BQC_TRY(jpass_fp32(df, ms->B32p.as<float>(), ms->w32.as<float>(), J, js));
+  } else if (j64) {
     BQC_TRY(jpass_fp64(df, J, js));
   } else {
     const dim3 jgrid((unsigned)((n + 1) / 2),
@@ -1535,8 +1619,16 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     BQC_LAUNCH_CHECK();
   }
   if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
-  BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, s));
-  df->mark(3, s);
+  // the SYRK on the higher-priority tensor-core stream (forked from the
+  // same point as J), so its persistent CTAs are placed before J's blocks
+  cudaStream_t ks = (df->side && df->tcs) ? df->tcs : s;
+  if (ks != s) BQC_CUDA_TRY(cudaStreamWaitEvent(ks, df->fork, 0));
+  BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, ks));
+  if (df->timing && df->ev[3]) cudaEventRecord(df->ev[3], ks);
+  if (ks != s) {
+    BQC_CUDA_TRY(cudaEventRecord(df->tjoin, ks));
+    BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->tjoin, 0));
+  }
   if (df->side) {
     BQC_CUDA_TRY(cudaEventRecord(df->join, df->side));
     BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->join, 0));
@@ -1776,6 +1868,8 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
     BQC_LAUNCH_CHECK();
     XpassParams p;
     p.rows = (int64_t)n * dm->bs;
+    p.row0 = 0;
+    p.wstride = p.rows;
     p.n = n;
     p.ldx = m.ldx;
     p.ncg = m.ncg;
