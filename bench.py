@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving run: Poisson stream of (H2O)_n solves, p50/p99 latency")
     ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-leg", type=int, default=6,
+                    help="requests per offered rate in the default line's serving leg (0: skip)")
+    ap.add_argument("--serve-low-rate", type=float, default=0.1,
+                    help="the sub-capacity offered rate of the serving leg (req/s)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-policy", choices=["backfill", "fifo"], default="backfill")
@@ -246,6 +250,44 @@ def config(mol, prec):
                   f"of split B shadows read by the X pass, {naux * n * (n + 1) / 2 * 8 / 1e9:.1f} GB "
                   "of FP64 B by the J pass)",
             "parallelism": "replicas"}
+
+
+def serve_leg(bqc, ctx, workload, nreq, rate, slots=8, prec=None, incremental=True,
+              policy=0, budget=150 * 10 ** 9, log=None):
+    """Submits the first `nreq` requests of the seed-2025 Poisson stream at
+    their arrival times (offered `rate` req/s) to one server and waits for
+    all; latency = completion - arrival (the server's submit time)."""
+    stream = workload.serving_stream(nreq=nreq, rate_hz=rate)
+    srv = bqc.Server(ctx, max_slots=slots, hbm_budget=budget, prec=prec, policy=policy,
+                     incremental=incremental)
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, n, rid) in stream:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((ta, n, srv.submit(workload.water_cluster(n, seed=rid))))
+    done = {}
+    while len(done) < len(tickets):
+        for (ta, n, t) in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+                    if log:
+                        print(f"[serve {rate} req/s] n={n} nbf={r['nbf']} status={r['status']} "
+                              f"iters={r['iterations']} (mixed {r['iterations_mixed']}) "
+                              f"wait={r['t_admit'] - r['t_submit']:.2f}s "
+                              f"run={r['t_done'] - r['t_admit']:.2f}s", file=log, flush=True)
+        time.sleep(0.02)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = sorted(done[t]["t_done"] - done[t]["t_submit"] for (_, _, t) in tickets)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"offered_req_per_s": rate, "requests": len(lat), "p50_ms": q(0.5) * 1e3,
+            "p99_ms": q(0.99) * 1e3, "solves_per_s": len(lat) / wall, "wall_s": wall,
+            "converged": sum(1 for t in done.values() if t["status"] == 0),
+            "sizes_n": [n for (_, n, _) in tickets]}
 
 
 def run_serve(args):
@@ -480,12 +522,14 @@ def run_screen_ablation(args):
         times[names[v]] = statistics.median(ts)
         outs.append(out.cpu() if v == 0 else out)
     same = [bool(torch.equal(outs[v].cpu(), outs[0])) for v in (1, 2)]
+    maxdiff = [float((outs[v].cpu() - outs[0]).abs().max()) for v in (1, 2)]
     cand, kept = df.screening()
     line = {"metric": "ms per screened 3-centre integral block", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"{mol.name} aux functions [0, {p1}) of Naux={basis.naux}, "
                                    f"N={basis.nbf}, Schwarz 1e-10 (direct-mode block)"},
             "ms": times, "bitwise_equal_to_sorted_prefix": same,
+            "max_abs_diff_to_sorted_prefix": maxdiff,
             "triplets_kept_fraction_all_aux": kept / max(1, cand),
             "speed_vs_sorted_prefix": {k: times["sorted_prefix"] / v for k, v in times.items()}}
     print(json.dumps(line), flush=True)
@@ -754,6 +798,23 @@ def main():
     line.update(extra)
     if not args.no_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(mol)
+    if args.serve_leg > 0 and world == 1:
+        # serving on a bounded prefix of the seed-2025 stream, after the
+        # (H2O)_64 handle is released (the 150 GB arena would not fit beside it)
+        df.close()
+        del J, K, J64, K64, C
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        sv = {}
+        for rate in (args.serve_rate, args.serve_low_rate):
+            sv[f"{rate:g}_req_per_s"] = serve_leg(bqc, ctx, workload, args.serve_leg, rate,
+                                                  prec=MIX, log=sys.stderr)
+        line["serve"] = {"prec": args.prec + " staged, incremental FP64 stage", "slots": 8,
+                         "hbm_budget_gb": 150, "policy": "backfill",
+                         "workload": f"first {args.serve_leg} requests of the seed-2025 Poisson "
+                                     "stream, (H2O)_n with n ~ U{2..48}, submitted at their "
+                                     "arrival times scaled to each offered rate",
+                         "legs": sv}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

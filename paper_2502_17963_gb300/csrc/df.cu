@@ -87,57 +87,51 @@ __global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
   }
 }
 
-// J pass over a packed FP32 copy of B (the split-FP16 build): rows of ld4
-// floats (Npair rounded up to 4, zero padded); each thread owns four
-// adjacent columns (one 16-byte load per P, eight in flight), multiplies and
-// sums in FP32 over runs of 32 P and adds the runs in FP64.  Half the bytes
-// of the FP64 pass and no FP64 arithmetic: the pass is bound by memory
-// parallelism, which beside the SYRK is what a J block gets.
-__global__ void __launch_bounds__(256) k_jpass32(const float *__restrict__ B,
-                                                 const float *__restrict__ w, int P0, int P1,
-                                                 int64_t ld4, int y0, double *__restrict__ Jp) {
-  const int64_t c4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (c4 >= ld4) return;
+// J pass over packed FP64 B for aux functions [P0, P1), partials into the
+// slices y0 .. y0 + gridDim.y - 1 (the two-half pipeline of the split-FP16
+// build); the same streaming scheme as k_jpass64.
+__global__ void __launch_bounds__(256) k_jpass64_range(const double *__restrict__ B,
+                                                       const double *__restrict__ w, int P0,
+                                                       int P1, int64_t npair, int y0,
+                                                       double *__restrict__ Jp) {
+  const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (c2 >= npair) return;
   const int per = (P1 - P0 + gridDim.y - 1) / gridDim.y;
   const int Pa = P0 + blockIdx.y * per, Pb = min(P1, Pa + per);
-  const float4 *b4 = reinterpret_cast<const float4 *>(B + c4);
-  const int64_t st = ld4 / 4;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int P = Pa;
-  while (P < Pb) {
-    const int P1 = min(Pb, P + 32);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    for (; P + 8 <= P1; P += 8) {
-      float4 v[8];
+  double *out = Jp + (int64_t)(y0 + blockIdx.y) * npair;
+  double a0 = 0.0, a1 = 0.0;
+  if (c2 + 1 < npair && (npair % 2 == 0)) {
+    const double2 *b2 = reinterpret_cast<const double2 *>(B + c2);
+    const int64_t st = npair / 2;
+    int P = Pa;
+    for (; P + 8 <= Pb; P += 8) {
+      double2 v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = __ldg(b4 + (int64_t)(P + k) * st);
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(b2 + (int64_t)(P + k) * st);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float wp = __ldg(w + P + k);
-        s0 = fmaf(wp, v[k].x, s0);
-        s1 = fmaf(wp, v[k].y, s1);
-        s2 = fmaf(wp, v[k].z, s2);
-        s3 = fmaf(wp, v[k].w, s3);
+        const double wp = __ldg(w + P + k);
+        a0 = fma(wp, v[k].x, a0);
+        a1 = fma(wp, v[k].y, a1);
       }
     }
-    for (; P < P1; ++P) {
-      const float4 v = __ldg(b4 + (int64_t)P * st);
-      const float wp = __ldg(w + P);
-      s0 = fmaf(wp, v.x, s0);
-      s1 = fmaf(wp, v.y, s1);
-      s2 = fmaf(wp, v.z, s2);
-      s3 = fmaf(wp, v.w, s3);
+    for (; P < Pb; ++P) {
+      const double2 v = __ldg(b2 + (int64_t)P * st);
+      const double wp = __ldg(w + P);
+      a0 = fma(wp, v.x, a0);
+      a1 = fma(wp, v.y, a1);
     }
-    a0 += s0;
-    a1 += s1;
-    a2 += s2;
-    a3 += s3;
+    out[c2] = a0;
+    out[c2 + 1] = a1;
+  } else {
+    for (int P = Pa; P < Pb; ++P) {
+      const double wp = __ldg(w + P);
+      a0 = fma(wp, B[(int64_t)P * npair + c2], a0);
+      if (c2 + 1 < npair) a1 = fma(wp, B[(int64_t)P * npair + c2 + 1], a1);
+    }
+    out[c2] = a0;
+    if (c2 + 1 < npair) out[c2 + 1] = a1;
   }
-  double *out = Jp + (int64_t)(y0 + blockIdx.y) * ld4 + c4;
-  out[0] = a0;
-  out[1] = a1;
-  out[2] = a2;
-  out[3] = a3;
 }
 
 // J[r][c] = sum_y Jp[y][pair(r, c)] (full symmetric N x N, chunks in order).
@@ -184,7 +178,6 @@ int jpass_fp64(Df *df, double *J, cudaStream_t s) {
   return BQC_OK;
 }
 
-int64_t jpass32_ld(int64_t npair) { return (npair + 3) / 4 * 4; }
 
 // Packed lower triangle of a symmetric N x N matrix with the off-diagonal
 // doubled: D2[mu(mu+1)/2 + nu] = (2 - delta_mu nu) D[mu][nu] (so that
@@ -226,30 +219,22 @@ int jfp64_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_
   return jpass_fp64(df, J, s);
 }
 
-int jpass_fp32_range(Df *df, const float *B32p, const float *w32, int P0, int P1, int y0,
-                     cudaStream_t s) {
-  const int64_t ld4 = jpass32_ld(df->npair);
-  const int sp = jpass_split(ld4, P1 - P0);
-  if (df->Jp.n < (size_t)(y0 + sp) * ld4 * 8) return BQC_E_INVALID;
-  k_jpass32<<<dim3((unsigned)((ld4 / 4 + 255) / 256), (unsigned)sp), 256, 0, s>>>(
-      B32p, w32, P0, P1, ld4, y0, df->Jp.as<double>());
+int jpass_fp64_range(Df *df, int P0, int P1, int y0, cudaStream_t s) {
+  const int64_t npair = df->npair;
+  const int sp = jpass_split(npair, P1 - P0);
+  if (df->Jp.n < (size_t)(y0 + sp) * npair * 8) return BQC_E_INVALID;
+  k_jpass64_range<<<dim3((unsigned)((npair / 2 + 256) / 256), (unsigned)sp), 256, 0, s>>>(
+      df->B64.as<double>(), df->w.as<double>(), P0, P1, npair, y0, df->Jp.as<double>());
   BQC_LAUNCH_CHECK();
   return BQC_OK;
 }
 
-int jpass_fp32_unpack(Df *df, int nslice, double *J, cudaStream_t s) {
+int jpass_unpack(Df *df, int nslice, double *J, cudaStream_t s) {
   const int n = df->basis->nbf;
-  // the chunk partials have row stride ld4 >= npair: sum them with that stride
-  k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(
-      df->Jp.as<double>(), nslice, jpass32_ld(df->npair), n, J);
+  k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(),
+                                                                         nslice, df->npair, n, J);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
-}
-
-int jpass_fp32(Df *df, const float *B32p, const float *w32, double *J, cudaStream_t s) {
-  const int naux = df->naux_loc;
-  BQC_TRY(jpass_fp32_range(df, B32p, w32, 0, naux, 0, s));
-  return jpass_fp32_unpack(df, jpass_split(jpass32_ld(df->npair), naux), J, s);
 }
 
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s) {

@@ -96,14 +96,10 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 // J = sum_P w_P B_P from the packed FP64 B and df->w (FP64), full symmetric.
 int jpass_fp64(Df *df, double *J, cudaStream_t s);
-// J = sum_P w32_P B32p_P over a packed FP32 copy of B (rows of jpass32_ld(Npair)).
-int64_t jpass32_ld(int64_t npair);
-int jpass_fp32(Df *df, const float *B32p, const float *w32, double *J, cudaStream_t s);
-// The same in pieces: partials of aux functions [P0, P1) into partial slices
-// starting at y0, then the sum of nslice slices into J.
-int jpass_fp32_range(Df *df, const float *B32p, const float *w32, int P0, int P1, int y0,
-                     cudaStream_t s);
-int jpass_fp32_unpack(Df *df, int nslice, double *J, cudaStream_t s);
+// The FP64 J pass in pieces: partials of aux functions [P0, P1) (df->w) into
+// partial slices starting at y0, then the sum of nslice slices into J.
+int jpass_fp64_range(Df *df, int P0, int P1, int y0, cudaStream_t s);
+int jpass_unpack(Df *df, int nslice, double *J, cudaStream_t s);
 int jpass_split(int64_t npair, int naux);
 // J[D] = sum_P (B_P : D) B_P in FP64 over the stored FP64 B for a symmetric
 // N x N matrix D (any sign), D2 an Npair scratch.

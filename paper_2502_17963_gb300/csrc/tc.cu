@@ -992,16 +992,6 @@ __global__ void k_expand_split16(const double *__restrict__ B, int n, int ld, in
   Bl[i] = __float2half_rn(l);
 }
 
-// Packed FP32 copy of B for the J pass of the split-FP16 build: rows of ld4
-// floats (Npair rounded up to 4), zero padded.
-__global__ void k_pack_f32(const double *__restrict__ B, int64_t npair, int64_t ld4, int np,
-                           float *__restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)np * ld4) return;
-  const int64_t P = i / ld4, c = i % ld4;
-  out[i] = c < npair ? (float)B[P * npair + c] : 0.0f;
-}
-
 // *out = max over rows of sum_c Bh[row][c]^2 (one warp per row; float bits).
 __global__ void __launch_bounds__(256) k_rowsq_max16(const __half *__restrict__ Bh, int64_t rows,
                                                      int ld, unsigned *out) {
@@ -1168,7 +1158,7 @@ size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow) {
     b += (size_t)2 * naux * n * m.ldx * 2;                           // Xh16, Xl16
     b += (size_t)2 * m.ldx * m.ld16 * 2 + (size_t)n * m.ldx * 4;     // C split, Cf
     b += (size_t)(nocc + 1) * 4 + 256;                               // statistics, scales
-    b += (size_t)naux * jpass32_ld((int64_t)n * (n + 1) / 2) * 4;   // packed FP32 B (J pass)
+    b += (size_t)jpass_split((int64_t)n * (n + 1) / 2, naux) * n * (n + 1) / 2 * 8;  // J halves
   } else {
     b += (size_t)2 * naux * n * m.ld * 4;                            // Bh, Bl
     b += (size_t)2 * naux * n * m.ldx * 4;                           // Xh, Xl
@@ -1184,12 +1174,11 @@ struct MixedState {
   DBuf Bl, Xl, Cl, Cf, wpart, w32;
   // FP16 split
   DBuf Bh16, Bl16, Xh16, Xl16, Ch16, Cl16, cstat, scale;
-  DBuf B32p;             // packed FP32 copy of B for the J pass
   int eB = 0;            // s_B = 2^eB
   double rownorm = 0.0;  // max_{P,mu} ||B_P,mu .||_2, unscaled, with a safety factor
   size_t bytes() const {
     return Bl.n + Xl.n + Cl.n + Cf.n + wpart.n + w32.n + Bh16.n + Bl16.n + Xh16.n + Xl16.n +
-           Ch16.n + Cl16.n + cstat.n + scale.n + B32p.n;
+           Ch16.n + Cl16.n + cstat.n + scale.n;
   }
 };
 
@@ -1312,17 +1301,12 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   std::memcpy(&maxsq, &hb, 4);
   // |B row| <= |Bh row| / (1 - 2^-11); the factor also covers the float sums
   ms->rownorm = std::sqrt((double)maxsq) / (double)sB * (1.0 + 1.0 / 256.0);
-  {  // packed FP32 B for the J pass, and room for its chunk partials
-    const int64_t ld4 = jpass32_ld(df->npair);
-    BQC_TRY(ms->B32p.alloc(ctx, (size_t)naux * ld4 * 4));
-    const int64_t tot = (int64_t)naux * ld4;
-    k_pack_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(df->B64.as<double>(), df->npair, ld4,
-                                                             naux, ms->B32p.as<float>());
-    BQC_LAUNCH_CHECK();
+  {  // room for the J partials of the two halves
     const int ph = naux / 2;
-    const size_t need = (size_t)std::max(jpass_split(ld4, naux),
-                                         jpass_split(ld4, std::max(1, ph)) +
-                                             jpass_split(ld4, naux - ph)) * ld4 * 8;
+    const size_t need = (size_t)std::max(jpass_split(df->npair, naux),
+                                         jpass_split(df->npair, std::max(1, ph)) +
+                                             jpass_split(df->npair, naux - ph)) *
+                        df->npair * 8;
     if (df->Jp.n < need) BQC_TRY(df->Jp.alloc(ctx, need));
   }
   BQC_TRY(ms->Xh16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
@@ -1532,15 +1516,16 @@ static int mixed_syrk(Df *df, int kind, int split, const CUtensorMap *Xh, const 
 }
 
 // w comes fused from the X pass in every mixed precision (FP32 row partials
-// of X C, summed in FP64).  The J pass then runs on the side stream,
-// concurrently with the SYRK: 3xTF32 reads the packed FP64 B (FP64 FMAs),
-// FP16x3 a packed FP32 copy of B (FP32 FMAs, half the bytes), single-pass
-// TF32 the TF32 shadow.  The precision of B in the J pass matters: with the
-// 22-bit split of B there, max|dJ| is only ~1e-6, but in a diffuse basis the
-// orthogonalisation amplifies it (by up to 1/sqrt(s_min)) into a DIIS error
-// of ~1e-4, which would set the mixed SCF's error floor; FP32 (24 bits, 4x
-// finer) keeps J's share of that floor below K's.  The error of the fused
-// w, a smooth Coulomb-like perturbation, stays ~1e-7.
+// of X C, summed in FP64).  The J pass then runs on the side stream beside
+// the tensor-core passes: the three-product builds read the packed FP64 B
+// with FP64 w (FP64 FMAs), single-pass TF32 reads the TF32 shadow.  The
+// precision of J matters: J = sum_P w_P B_P cancels heavily, and in a
+// diffuse basis the orthogonalisation amplifies its error (by up to
+// 1/sqrt(s_min)) into the DIIS error: the 22-bit split of B there set the
+// mixed SCF's floor at ~2e-3, and a packed FP32 B with FP32 w at ~1e-2
+// (measured), against ~1e-4 from K; with FP64 B and w the J share is
+// ~3e-7.  The error of the fused w, a smooth Coulomb-like perturbation,
+// stays ~1e-7.
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s) {
   MixedState *ms = df->mixed.get();
   if (!ms) return BQC_E_INVALID;
@@ -1556,7 +1541,7 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   const Basis *b = df->basis;
   const int n = b->nbf, naux = df->naux_loc;
   const int64_t rows = (int64_t)naux * n;
-  const bool j64 = split == 3 && df->B64.p && kind == kKindTF32;
+  const bool j64 = split == 3 && df->B64.p;
   if (kind == kKindF16 && df->side && df->tcs && naux >= 2) {
     // Two halves of the aux index on the tensor-core stream: X pass (h1),
     // X pass (h2), SYRK, back to back; the J pass of each half follows it on
@@ -1580,12 +1565,12 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, ts));
     if (df->timing && df->ev[3]) cudaEventRecord(df->ev[3], ts);
     BQC_CUDA_TRY(cudaEventRecord(df->tjoin, ts));
-    const int sp1 = jpass_split(jpass32_ld(df->npair), Ph);
+    const int sp1 = jpass_split(df->npair, Ph);
     BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork, 0));
-    BQC_TRY(jpass_fp32_range(df, ms->B32p.as<float>(), ms->w32.as<float>(), 0, Ph, 0, js));
+    BQC_TRY(jpass_fp64_range(df, 0, Ph, 0, js));
     BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork2, 0));
-    BQC_TRY(jpass_fp32_range(df, ms->B32p.as<float>(), ms->w32.as<float>(), Ph, naux, sp1, js));
-    BQC_TRY(jpass_fp32_unpack(df, sp1 + jpass_split(jpass32_ld(df->npair), naux - Ph), J, js));
+    BQC_TRY(jpass_fp64_range(df, Ph, naux, sp1, js));
+    BQC_TRY(jpass_unpack(df, sp1 + jpass_split(df->npair, naux - Ph), J, js));
     if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
     BQC_CUDA_TRY(cudaEventRecord(df->join, js));
     BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->tjoin, 0));
@@ -1604,9 +1589,7 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     BQC_CUDA_TRY(cudaStreamWaitEvent(df->side, df->fork, 0));
     js = df->side;
   }
-  if (kind == kKindF16) {
-    BQC_TRY(jpass_fp32(df, ms->B32p.as<float>(), ms->w32.as<float>(), J, js));
-  } else if (j64) {
+  if (j64) {
     BQC_TRY(jpass_fp64(df, J, js));
   } else {
     const dim3 jgrid((unsigned)((n + 1) / 2),
