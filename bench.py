@@ -72,7 +72,10 @@ def parse():
                     help="time the three survivor compactions of the screened 3-centre "
                          "integrals on one aux block of (H2O)_128 (default) at tau = 1e-10")
     ap.add_argument("--mp2", action="store_true",
-                    help="DF-MP2 energy after an SCF at --waters (default (H2O)_16)")
+                    help="DF-MP2 energy after a staged SCF at --mp2-waters")
+    ap.add_argument("--mp2-waters", type=int, default=32, help="--mp2: cluster size")
+    ap.add_argument("--mp2-prec", choices=["f64", "f16x3"], default="f16x3",
+                    help="--mp2: FP64 DFMA pair blocks or split-FP16 tensor-core pair blocks")
     return ap.parse_args()
 
 
@@ -545,21 +548,25 @@ def run_mp2(args):
     from paper_2502_17963_gb300 import _build
     _build.build()
     torch.cuda.set_device(0)
-    nw = args.waters if args.waters != 64 else 16
+    nw = args.mp2_waters
     mol = workload.water_cluster(nw)
     ctx = bqc.Context(0)
     basis = bqc.Basis(ctx, mol)
     df = bqc.DF(ctx, basis, mode=bqc.DF_STORED, keep_fp32=bqc.SHADOW_F16)
     r = bqc.scf_run(ctx, df, prec=bqc.PREC_MIXED_F16X3, incremental=True, keep_arrays=True)
     C, eps = r["C"].contiguous(), r["eps"].contiguous()
-    bqc.mp2(df, C, eps)  # warm
+    mp = bqc.PREC_MIXED_F16X3 if args.mp2_prec == "f16x3" else bqc.PREC_FP64
+    bqc.mp2(df, C, eps, prec=mp)  # warm
     torch.cuda.synchronize()
     clocks = ClockSampler(gpu_index(0))
     clocks.start()
     t0 = time.perf_counter()
-    e2 = bqc.mp2(df, C, eps)
+    e2 = bqc.mp2(df, C, eps, prec=mp)
     dt = time.perf_counter() - t0
     clk = clocks.stop()
+    e2_64 = None
+    if mp != bqc.PREC_FP64 and nw <= 32:
+        e2_64 = bqc.mp2(df, C, eps, prec=bqc.PREC_FP64)
     n, naux, no = basis.nbf, basis.naux, basis.nocc
     nv = r["nmo"] - no
     bi = max(1, min(16, no, int((1 << 27) ** 0.5 / max(1, nv))))
@@ -569,18 +576,31 @@ def run_mp2(args):
         for j0 in range(0, i0 + 1, bi):
             nj = min(bi, no - j0)
             pair_flops += 2.0 * ni * nv * nj * nv * naux
-    flops = 2.0 * naux * n * n * no + 2.0 * naux * n * no * nv + pair_flops
+    tflops = 2.0 * naux * n * n * no + 2.0 * naux * n * no * nv  # FP64 MO transform
+    flops = tflops + pair_flops
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 DFMA units per SM at the max SM clock
-    line = {"metric": "s per DF-MP2 energy (FP64)", "value": dt, "unit": "s",
-            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+    pk, pk_src = peaks()
+    if mp == bqc.PREC_FP64:
+        roof = {"bound": "alu", "achieved": flops / dt / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp64_peak,
+                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flop": flops}
+    else:
+        t_tr = tflops / (fp64_peak * 1e12 * 0.9)  # the FP64 transform at the DFMA rate
+        t_pair = max(1e-9, dt - t_tr)
+        sust = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        roof = {"bound": "tensor", "kernel": "k_gemm_nt<f16> (pair blocks, 3 products)",
+                "achieved": pair_flops / t_pair / 1e12, "peak": sust, "unit": "TFLOP/s",
+                "frac": pair_flops / t_pair / 1e12 / sust,
+                "frac_issued": 3 * pair_flops / t_pair / 1e12 / sust,
+                "note": "pair-block time = total - FP64 transform at 0.9 of the DFMA rate "
+                        f"({t_tr:.2f} s estimated)", "peak_source": f"{pk_src}: bf16 sustained"}
+    line = {"metric": f"s per DF-MP2 energy ({args.mp2_prec})", "value": dt, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": args.mp2_prec,
             "config": {"workload": f"{mol.name} DF-MP2 after the staged SCF, N={n}, Naux={naux}, "
                                    f"nocc={no}, nvir={nv}"},
-            "e2_Eh": e2, "e_scf_Eh": r["energy"],
-            "roofline": {"bound": "alu", "achieved": flops / dt / 1e12, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp64_peak,
-                         "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                         "algorithmic_flop": flops},
-            "clocks": clk}
+            "e2_Eh": e2, "e2_fp64_Eh": e2_64,
+            "e_scf_Eh": r["energy"], "roofline": roof, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

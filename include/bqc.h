@@ -280,7 +280,10 @@ int bqc_df_phase_ms(bqc_df *df, float *ms, int n);
  * df: a stored-mode handle.  C_dev: N x nmo row-major canonical orbitals
  * (columns; the first nocc occupied, the rest virtual), eps_dev: their nmo
  * orbital energies (bqc_scf_run's C_dev / eps_dev outputs have this layout).
- * prec: BQC_PREC_FP64 (DFMA GEMMs); other precisions BQC_E_UNSUPPORTED.
+ * prec: BQC_PREC_FP64 (every GEMM on the DFMA path) or BQC_PREC_MIXED_F16X3
+ * (the MO transform in FP64, the (ia|jb) blocks as split-FP16 tensor-core
+ * GEMMs with FP32 accumulation in short chains and FP64 blocks, ~2^-22
+ * relative per integral); other precisions BQC_E_UNSUPPORTED.
  * Writes *e2 (host).  Allocates its working memory from the context
  * (Naux * nocc * nvir doubles and a block of (ia|jb) of at most 1 GiB) and
  * synchronises the stream; reuses the handle's X buffer, so it must not

@@ -112,6 +112,15 @@ int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cud
 int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s);
 int jk_direct(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 size_t df_stored_bytes(int n, int naux, int nocc, int shadow);
+// Split-FP16 tensor-core pair blocks of DF-MP2 (tc.cu).
+struct Mp2Tc;
+struct Mp2TcDeleter {
+  void operator()(Mp2Tc *p) const;
+};
+int mp2_tc_setup(Ctx *ctx, const double *Bt, int naux, int nocc, int nv, int *flag,
+                 std::unique_ptr<Mp2Tc, Mp2TcDeleter> &out, cudaStream_t s);
+int mp2_tc_block(Mp2Tc *m, int nv, int i0, int ni, int j0, int nj, double *V, int64_t ldv,
+                 int *flag, cudaStream_t s);
 int jk4c_setup(Df *df, cudaStream_t s);
 int jk_4c(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 

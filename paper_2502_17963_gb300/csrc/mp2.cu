@@ -7,11 +7,13 @@
 //   E2 = sum_{ijab} (ia|jb) [2 (ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b)
 // (Szabo & Ostlund Eq. 6.74) is accumulated with the denominator applied in
 // place, one block of occupied pairs at a time, so no four-index array is
-// ever held.  FP64 path: the register-blocked DFMA GEMM of gemm64.cuh.
+// ever held.  FP64: the register-blocked DFMA GEMM of gemm64.cuh;
+// MIXED_F16X3: the pair blocks on the tensor cores (tc.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "bqc_internal.h"
@@ -78,8 +80,11 @@ static int mp2_block(int nocc, int nvir) {
   return std::max(1, std::min({bi, 16, nocc}));
 }
 
-static int mp2_fp64(Df *df, const double *C, const double *eps, int nmo, double *e2,
-                    cudaStream_t s) {
+// prec FP64: every GEMM on the DFMA path; MIXED_F16X3: the MO transform in
+// FP64, the pair blocks as split-FP16 tensor-core GEMMs (FP32 accumulation in
+// short chains, float-float drains, FP64 blocks), the energy in FP64.
+static int mp2_run(Df *df, const double *C, const double *eps, int nmo, int prec, double *e2,
+                   cudaStream_t s) {
   const Basis *b = df->basis;
   const int n = b->nbf, naux = b->naux, no = b->nocc, nv = nmo - no;
   Ctx *ctx = df->ctx;
@@ -120,6 +125,12 @@ static int mp2_fp64(Df *df, const double *C, const double *eps, int nmo, double 
     t.bsC = (int64_t)no * nv;
     t.batch = naux;
     BQC_TRY(launch_gemm64(kAT, false, t, s));
+    std::unique_ptr<Mp2Tc, Mp2TcDeleter> tcs;
+    if (prec == BQC_PREC_MIXED_F16X3) {
+      BQC_TRY(mp2_tc_setup(ctx, Bt.as<double>(), naux, no, nv, ctx->flag, tcs, s));
+      BQC_CUDA_TRY(cudaStreamSynchronize(s));
+      Bt.release();  // the split operand replaces it
+    }
     const int bi = mp2_block(no, nv);
     BQC_TRY(V.alloc(ctx, (size_t)bi * nv * bi * nv * 8));
     const int64_t ldt = (int64_t)no * nv;
@@ -128,6 +139,14 @@ static int mp2_fp64(Df *df, const double *C, const double *eps, int nmo, double 
       for (int j0 = 0; j0 <= i0; j0 += bi) {
         const int nj = std::min(bi, no - j0);
         // V[(ii,a)][(jj,b)] = sum_P Bt[P][i0+ii][a] Bt[P][j0+jj][b]
+        if (tcs) {
+          BQC_TRY(mp2_tc_block(tcs.get(), nv, i0, ni, j0, nj, V.as<double>(), (int64_t)nj * nv,
+                               ctx->flag, s));
+          k_mp2_pairs<<<dim3((unsigned)ni, (unsigned)nj), 256, 0, s>>>(
+              V.as<double>(), (int64_t)nj * nv, i0, j0, nv, eps, no, ep.as<double>());
+          BQC_LAUNCH_CHECK();
+          continue;
+        }
         Gemm64Args v;
         v.M = ni * nv;
         v.N = nj * nv;
@@ -167,7 +186,8 @@ extern "C" int bqc_mp2(bqc_df *df, const double *C_dev, const double *eps_dev, i
   if (nmo < df->basis->nocc || nmo > df->basis->nbf) return BQC_E_INVALID;
   BQC_CUDA_TRY(cudaSetDevice(df->ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == BQC_PREC_FP64) return mp2_fp64(df, C_dev, eps_dev, nmo, e2, s);
+  if (prec == BQC_PREC_FP64 || prec == BQC_PREC_MIXED_F16X3)
+    return mp2_run(df, C_dev, eps_dev, nmo, prec, e2, s);
   set_error("bqc_mp2: precision not available", __FILE__, __LINE__);
   return BQC_E_UNSUPPORTED;
 }

@@ -645,6 +645,178 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
+// C = scale * A B^T for row ranges of two K-major split-FP16 operands (the
+// DF-MP2 pair blocks: rows (i, a) of the MO tensor against rows (j, b),
+// contraction over the aux index).  Persistent over output tiles; tile it ->
+// (it / nt, it % nt); each tile is one K loop (no aux chunks), drained from
+// TMEM in short chains into float-float registers as in the SYRK, and
+// written in FP64.
+struct GemmNtParams {
+  int mt, nt;              // output tiles along M and N
+  int64_t a_row0, b_row0;  // first rows of the A and B ranges in the maps
+  int kblocks;             // k-blocks of 64 elements
+  int stages;
+  double *out;
+  int64_t ldo;
+  int mvalid, nvalid;      // valid rows / columns of C
+  double scale;
+  int *flag;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_nt(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+              const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
+              const GemmNtParams p) {
+  using KD = Kind<KIND>;
+  constexpr int KE = KD::kElems;
+  constexpr uint32_t stage_bytes = 4 * kAStage;  // [Ah][Bh][Al][Bl]
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
+  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = p.mt * p.nt;
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapAh);
+    prefetch_tmap(&mapAl);
+    prefetch_tmap(&mapBh);
+    prefetch_tmap(&mapBl);
+    for (int st = 0; st < p.stages; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tslot), 512);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t kg = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int tm = it / p.nt, tn = it % p.nt;
+        const int ra = (int)(p.a_row0 + (int64_t)tm * kBM), rb = (int)(p.b_row0 + (int64_t)tn * kBM);
+        for (int kb = 0; kb < p.kblocks && ok; ++kb, ++kg) {
+          const int st = (int)(kg % p.stages);
+          if (kg >= p.stages)
+            ok = mbar_wait(empty0 + 8 * st, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 41);
+          if (!ok) break;
+          const uint32_t a = sbase + st * stage_bytes, bar = full0 + 8 * st;
+          mbar_arrive_expect_tx(bar, stage_bytes);
+          tma_load_2d(a, &mapAh, bar, kb * KE, ra);
+          tma_load_2d(a + kAStage, &mapBh, bar, kb * KE, rb);
+          tma_load_2d(a + 2 * kAStage, &mapAl, bar, kb * KE, ra);
+          tma_load_2d(a + 3 * kAStage, &mapBl, bar, kb * KE, rb);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = KD::idesc(kBM, kBM);
+      int64_t kg = 0, g = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        for (int kb0 = 0; kb0 < p.kblocks && ok; kb0 += kGroupKbS, ++g) {
+          const int b = (int)(g & 1);
+          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 44);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tbase + b * kBM;
+          const int kb1 = min(p.kblocks, kb0 + kGroupKbS);
+          for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
+            const int st = (int)(kg % p.stages);
+            ok = mbar_wait(full0 + 8 * st, (uint32_t)((kg / p.stages) & 1), p.flag, 42);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = sbase + st * stage_bytes, bh = ah + kAStage;
+            const uint32_t al = ah + 2 * kAStage, bl = ah + 3 * kAStage;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {  // cross terms first
+              const uint32_t acc = ((kb - kb0) | k4) != 0;
+              KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(bl + k4 * 32), acc, idesc);
+              KD::mma(d, sdesc_sw128(al + k4 * 32), sdesc_sw128(bh + k4 * 32), 1, idesc);
+            }
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4)
+              KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(bh + k4 * 32), 1, idesc);
+            mma_commit(empty0 + 8 * st);
+          }
+          mma_commit(tfull0 + 8 * b);
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int64_t g = 0;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      const int tm = it / p.nt, tn = it % p.nt;
+      float hi[kSyCols];
+#pragma unroll
+      for (int c = 0; c < kSyCols; ++c) hi[c] = 0.0f;
+      {
+        float z[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kSyCols; c += 16)
+          tmem_st16(tbase + lane_base + kLoCol + h * kSyCols + c, z);
+      }
+      for (int kb0 = 0; kb0 < p.kblocks; kb0 += kGroupKbS, ++g) {
+        const int b = (int)(g & 1);
+        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 43);
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t ta = tbase + lane_base + b * kBM + h * kSyCols;
+        const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+#pragma unroll
+        for (int c = 0; c < kSyCols; c += 16) {
+          float v[16], lo[16];
+          tmem_ld16(ta + c, v);
+          tmem_ld16(tl + c, lo);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {  // two-sum: (hi, lo) += v
+            const float sm = hi[c + i] + v[i];
+            const float bp = sm - hi[c + i];
+            lo[i] += (hi[c + i] - (sm - bp)) + (v[i] - bp);
+            hi[c + i] = sm;
+          }
+          tmem_st16(tl + c, lo);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      }
+      const int r = tm * kBM + q * 32 + lane;
+      const int c0 = tn * kBM + h * kSyCols;
+      const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+#pragma unroll
+      for (int c = 0; c < kSyCols; c += 16) {
+        float lo[16];
+        tmem_ld16(tl + c, lo);
+        if (ok && r < p.mvalid) {
+          double *dst = p.out + (int64_t)r * p.ldo + c0 + c;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + c + i < p.nvalid) dst[i] = ((double)hi[c + i] + (double)lo[i]) * p.scale;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 // K = sum over chunks of the FP64 partial tiles, symmetric.  One block per
 // (lower tile, 32-row strip): sums into shared memory, writes the strip and
 // its mirror image coalesced.
@@ -1958,3 +2130,118 @@ extern "C" int bqc_wait_selftest(bqc_ctx *ctx, long long cycles, bqc_stream_t st
   BQC_LAUNCH_CHECK();
   return ctx->check_flag(s);
 }
+
+// ----------------------------------------------------- DF-MP2 pair GEMMs --
+
+namespace bqc {
+
+// Bt ([P][q], q = (i, a), FP64) -> A[q][P] = split FP16 of s * Bt, the rows
+// of (ia|jb)'s K-major operands (P padded with zeros to ldp), through a
+// 32 x 32 shared-memory transpose (coalesced reads over q, writes over P).
+__global__ void k_transpose_split16(const double *__restrict__ Bt, int naux, int64_t Q, int ldp,
+                                    double scale, __half *__restrict__ Ah,
+                                    __half *__restrict__ Al) {
+  __shared__ float t[32][33];
+  const int64_t q0 = (int64_t)blockIdx.x * 32;
+  const int p0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int P = p0 + r;
+    const int64_t q = q0 + threadIdx.x;
+    t[r][threadIdx.x] = (P < naux && q < Q) ? (float)(Bt[(int64_t)P * Q + q] * scale) : 0.0f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t q = q0 + r;
+    const int P = p0 + threadIdx.x;
+    if (q < Q && P < ldp) {
+      const float f = t[threadIdx.x][r];
+      const __half h = __float2half_rn(f);
+      Ah[q * ldp + P] = h;
+      Al[q * ldp + P] = __float2half_rn(f - __half2float(h));
+    }
+  }
+}
+
+struct Mp2Tc {
+  int naux = 0, ldp = 0;
+  int64_t Q = 0;
+  double inv_scale2 = 1.0;
+  int stages = 0;
+  size_t smem = 0;
+  DBuf Ah, Al;
+  CUtensorMap mapAh, mapAl;
+};
+
+void Mp2TcDeleter::operator()(Mp2Tc *p) const { delete p; }
+
+int mp2_tc_setup(Ctx *ctx, const double *Bt, int naux, int nocc, int nv, int *flag,
+                 std::unique_ptr<Mp2Tc, Mp2TcDeleter> &out, cudaStream_t s) {
+  Mp2Tc *m = new Mp2Tc();
+  out.reset(m);
+  m->naux = naux;
+  m->Q = (int64_t)nocc * nv;
+  m->ldp = round_up(naux, 8);
+  // scale: largest |B_P,ia| to at most 2^14
+  DBuf stat;
+  BQC_TRY(stat.alloc(ctx, 256));
+  BQC_CUDA_TRY(cudaMemsetAsync(stat.p, 0, 256, s));
+  const int64_t nb = (int64_t)naux * m->Q;
+  const unsigned grid = (unsigned)std::min<int64_t>((nb + 255) / 256, (int64_t)sm_count() * 8);
+  k_absmax_f64<<<std::max(1u, grid), 256, 0, s>>>(Bt, nb, stat.as<unsigned>());
+  BQC_LAUNCH_CHECK();
+  unsigned hb = 0;
+  BQC_CUDA_TRY(cudaMemcpyAsync(&hb, stat.p, 4, cudaMemcpyDeviceToHost, s));
+  BQC_CUDA_TRY(cudaStreamSynchronize(s));
+  float mx = 0.0f;
+  std::memcpy(&mx, &hb, 4);
+  int e = 0;
+  if (mx > 0.0f) {
+    const double mt = std::frexp((double)mx, &e);
+    if (mt == 0.5) --e;
+  }
+  const double sc = std::ldexp(1.0, 14 - e);
+  m->inv_scale2 = 1.0 / (sc * sc);
+  BQC_TRY(m->Ah.alloc(ctx, (size_t)m->Q * m->ldp * 2));
+  BQC_TRY(m->Al.alloc(ctx, (size_t)m->Q * m->ldp * 2));
+  k_transpose_split16<<<dim3((unsigned)((m->Q + 31) / 32), (unsigned)((m->ldp + 31) / 32)),
+                        dim3(32, 8), 0, s>>>(Bt, naux, m->Q, m->ldp, sc, m->Ah.as<__half>(),
+                                             m->Al.as<__half>());
+  BQC_LAUNCH_CHECK();
+  const uint64_t dims[2] = {(uint64_t)m->ldp, (uint64_t)m->Q};
+  const uint64_t str[1] = {(uint64_t)m->ldp * 2};
+  const uint32_t box[2] = {64, kBM};
+  BQC_TRY(make_tmap_f16(&m->mapAh, m->Ah.p, 2, dims, str, box));
+  BQC_TRY(make_tmap_f16(&m->mapAl, m->Al.p, 2, dims, str, box));
+  const size_t avail = 232448 - 1024 - 256;
+  m->stages = (int)std::min<size_t>(8, avail / (4 * kAStage));
+  m->smem = (size_t)m->stages * 4 * kAStage + 1024 + 256;
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_gemm_nt<kKindF16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem));
+  (void)flag;
+  return BQC_OK;
+}
+
+// V[(ii, a)][(jj, b)] = sum_P B_P,(i0+ii) a B_P,(j0+jj) b for ni x nj occupied
+// orbitals, FP64 out (ldv), from the split FP16 operand.
+int mp2_tc_block(Mp2Tc *m, int nv, int i0, int ni, int j0, int nj, double *V, int64_t ldv,
+                 int *flag, cudaStream_t s) {
+  GemmNtParams p;
+  p.mvalid = ni * nv;
+  p.nvalid = nj * nv;
+  p.mt = (p.mvalid + kBM - 1) / kBM;
+  p.nt = (p.nvalid + kBM - 1) / kBM;
+  p.a_row0 = (int64_t)i0 * nv;
+  p.b_row0 = (int64_t)j0 * nv;
+  p.kblocks = (m->ldp + 63) / 64;
+  p.stages = m->stages;
+  p.out = V;
+  p.ldo = ldv;
+  p.scale = m->inv_scale2;
+  p.flag = flag;
+  const int grid = std::min(sm_count(), p.mt * p.nt);
+  k_gemm_nt<kKindF16><<<grid, kThreads, m->smem, s>>>(m->mapAh, m->mapAl, m->mapAh, m->mapAl, p);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+}  // namespace bqc

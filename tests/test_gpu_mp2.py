@@ -6,7 +6,11 @@
   * end to end: the GPU's own SCF orbitals (bqc_scf_run) into bqc_mp2 against
     the oracle's SCF + MP2, to 1e-8 Eh;
   * the degenerate case of no virtual orbitals (nmo = nocc) gives E2 = 0, and
-    a direct-mode handle is refused.
+    a direct-mode handle is refused;
+  * MIXED_F16X3 (pair blocks on the tensor cores, split FP16): within 2^-18
+    of the absolute sum of the MP2 terms, sum |(ia|jb)[2(ia|jb) - (ib|ja)] /
+    (e_i + e_j - e_a - e_b)| (the integrals carry ~2^-22 relative rounding and
+    the energy is linear in each of them to first order).
 """
 import numpy as np
 import pytest
@@ -72,3 +76,27 @@ def test_mp2_edge_cases(gpu_ctx, bqc):
     with pytest.raises(bqc.BqcError) as e:
         bqc.mp2(dd, torch.tensor(r.C, device="cuda"), torch.tensor(r.eps, device="cuda"))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("name", ["h2o", "w3", "w8"])
+def test_mp2_f16x3_against_oracle(gpu_ctx, bqc, name):
+    import torch
+    mol = workload.molecule_for(name)
+    basis = bqc.Basis(gpu_ctx, mol)
+    df = bqc.DF(gpu_ctx, basis, keep_fp32=False)
+    B, r = _oracle_scf(mol)
+    no = mol.nocc
+    ovov = oracle.ovov_df(B, r.C, no)
+    e_o = oracle.mp2_energy(ovov, r.eps, no)
+    eo, ev = r.eps[:no], r.eps[no:]
+    den = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] \
+        - ev[None, None, None, :]
+    absum = float(np.sum(np.abs(ovov * (2.0 * ovov - ovov.transpose(0, 3, 2, 1)) / den)))
+    Cg, eg = torch.tensor(r.C, device="cuda"), torch.tensor(r.eps, device="cuda")
+    e_g = bqc.mp2(df, Cg, eg, prec=bqc.PREC_MIXED_F16X3)
+    e_g2 = bqc.mp2(df, Cg, eg, prec=bqc.PREC_MIXED_F16X3)
+    ratio = abs(e_g - e_o) / absum
+    print(f"{name}: F16X3 E2 {e_g:.12f} oracle {e_o:.12f} diff {e_g - e_o:.2e} "
+          f"(ratio to the absolute term sum {ratio:.2e})")
+    assert e_g == e_g2  # deterministic: fixed-order reductions, no atomics
+    assert ratio < 2.0 ** -18
