@@ -357,7 +357,11 @@ enum { BQC_SWITCH_NONE = 0, BQC_SWITCH_STAGE_TOL = 1, BQC_SWITCH_FLOOR = 2 };
  * the first stage's mixed precision, so the rounding error of F_k scales
  * with |D_k - D_a|, not with |D|; in stored mode the Coulomb part J[dD] is
  * instead formed in FP64 from dD itself (two streaming passes over the FP64
- * B), which avoids the cancellation between the J of V+ and of V-.  Anchors (full FP64 builds) are made at
+ * B), which avoids the cancellation between the J of V+ and of V-; and with
+ * MIXED_F16X3 on a stored handle K[dD] is a rank-2k update: the occupied
+ * orbitals are rotated onto the anchor's (orthogonal Procrustes in the S
+ * metric), dD = Cw Cd^T + Cd Cw^T with Cd the small orbital difference, and
+ * the error of K[dD] scales with |Cd|.  Anchors (full FP64 builds) are made at
  * the switch, when the DIIS error first falls below 100 x diis_tol, after
  * 10 increments, and on every iteration that would converge: an
  * incremental iteration with max|e| < diis_tol and a stable energy is

@@ -6,6 +6,9 @@
 
 namespace bqc {
 
+// Aux pieces of the split-FP16 build's X pass (each followed by its J pass).
+constexpr int kJPieces = 4;
+
 struct MixedState;
 size_t mixed_bytes(const MixedState *ms);
 struct MixedDeleter {
@@ -67,12 +70,15 @@ struct Df {
   cudaStream_t side = nullptr;
   cudaStream_t tcs = nullptr;  // tensor-core stream, one priority level above side
   cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, prep = nullptr, tjoin = nullptr;
+  cudaEvent_t piece[kJPieces] = {};  // end of each X-pass piece (split-FP16 pipeline)
   ~Df() {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
     if (fork2) cudaEventDestroy(fork2);
     if (prep) cudaEventDestroy(prep);
+    for (auto &e : piece)
+      if (e) cudaEventDestroy(e);
     if (tjoin) cudaEventDestroy(tjoin);
     if (tcs) cudaStreamDestroy(tcs);
     if (join) cudaEventDestroy(join);
@@ -93,6 +99,9 @@ size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow);
 int mixed_ld(int n);  // row length of the TF32 shadow (N rounded up to 4)
 int mixed_setup(Df *df, int shadow, cudaStream_t s);
 int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
+// K of the symmetric density Cw Cd^T + Cd Cw^T (N x nocc row-major inputs)
+// on the split-FP16 tensor cores; BQC_E_UNSUPPORTED without FP16 shadows.
+int jk_k_rank2(Df *df, const double *Cw, const double *Cd, double *K, cudaStream_t s);
 int jk_fp64_stored(Df *df, const double *C, double *J, double *K, cudaStream_t s);
 // J = sum_P w_P B_P from the packed FP64 B and df->w (FP64), full symmetric.
 int jpass_fp64(Df *df, double *J, cudaStream_t s);

@@ -85,6 +85,18 @@ __global__ void k_eig_factor(int n, const double *U, const double *ev, int k0, i
   V[i] = c < cnt ? U[(int64_t)(k0 + c) * n + nu] * sqrt(fabs(ev[k0 + c])) : 0.0;
 }
 
+// Cw = (Ca + Ct) / 2, Cd = Ct - Ca (row-major n x no) from column-major Ca,
+// Ct (n x no): the midpoint and difference of two sets of occupied orbitals.
+__global__ void k_procrustes_pair(int n, int no, const double *Ca, const double *Ct, double *Cw,
+                                  double *Cd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * no) return;
+  const int64_t r = i / no, c = i % no;
+  const double a = Ca[c * n + r], t = Ct[c * n + r];
+  Cw[i] = 0.5 * (a + t);
+  Cd[i] = t - a;
+}
+
 // F = Fref + 2 (Jp - Jm) - (Kp - Km)
 __global__ void k_inc_fock(int64_t n, const double *Fref, const double *Jp, const double *Jm,
                            const double *Kp, const double *Km, double *F) {
@@ -255,10 +267,25 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   const bool inc_on = o.incremental != 0 && o.prec != BQC_PREC_FP64;
   const int mixed_prec = o.prec;
   DBuf Facc, Dref, Dk, Vp, Vm, J2, K2, evd, Jx, D2p;
+  // rank-2k increments (split-FP16 stored handles): the anchor's occupied
+  // orbitals, the Procrustes rotation and its work space
+  const bool rank2 = inc_on && mixed_prec == BQC_PREC_MIXED_F16X3 &&
+                     df->mode == BQC_DF_STORED && df->B64.p && df->mixed && !df->is_shard();
+  DBuf Ca, Sca, Mo, Uo, VTo, So, Ro, Ct, svdw, svdinfo;
+  int svd_lwork = 0;
   if (inc_on) {
     for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2, &Jx}) BQC_TRY(p->alloc(ctx, nn * 8));
     BQC_TRY(evd.alloc(ctx, (size_t)n * 8));
     BQC_TRY(D2p.alloc(ctx, (size_t)n * (n + 1) / 2 * 8));
+  }
+  if (rank2) {
+    const size_t on = (size_t)n * no * 8, oo = (size_t)no * no * 8;
+    for (DBuf *p : {&Ca, &Sca, &Ct}) BQC_TRY(p->alloc(ctx, on));
+    for (DBuf *p : {&Mo, &Uo, &VTo, &Ro}) BQC_TRY(p->alloc(ctx, oo));
+    BQC_TRY(So.alloc(ctx, (size_t)no * 8));
+    BQC_SOLVER_TRY(cusolverDnDgesvd_bufferSize(w.sol, no, no, &svd_lwork));
+    BQC_TRY(svdw.alloc(ctx, (size_t)std::max(1, svd_lwork) * 8));
+    BQC_TRY(svdinfo.alloc(ctx, sizeof(int)));
     BQC_TRY(Vp.alloc(ctx, (size_t)n * no * 8));
     BQC_TRY(Vm.alloc(ctx, (size_t)n * no * 8));
   }
@@ -289,6 +316,45 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     // cancellation between the two signed parts
     const bool jexact = df->mode == BQC_DF_STORED && df->B64.p;
     if (jexact) BQC_TRY(jfp64_of_density(df, t1.as<double>(), D2p.as<double>(), Jx.as<double>(), s));
+    if (rank2) {
+      // Exchange part as a rank-2k update: rotate the current occupied
+      // orbitals Ck onto the anchor's Ca (orthogonal Procrustes in the S
+      // metric: M = Ck^T S Ca = U s V^T, R = U V^T, Ct = Ck R, so that
+      // Ct Ct^T = D_k), then dD = Cw Cd^T + Cd Cw^T with Cw = (Ca + Ct) / 2
+      // and Cd = Ct - Ca small; K[dD] from W = B Cw and DY = B Cd carries
+      // rounding relative to |W||DY|, not to |D|.
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, no, n, &one, S.as<double>(),
+                               n, Ca.as<double>(), n, &zero, Sca.as<double>(), n));
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_T, CUBLAS_OP_N, no, no, n, &one, Cc.as<double>(),
+                               n, Sca.as<double>(), n, &zero, Mo.as<double>(), no));
+      BQC_SOLVER_TRY(cusolverDnDgesvd(w.sol, 'A', 'A', no, no, Mo.as<double>(), no,
+                                      So.as<double>(), Uo.as<double>(), no, VTo.as<double>(), no,
+                                      svdw.as<double>(), svd_lwork, nullptr,
+                                      svdinfo.as<int>()));
+      int hinfo = 0;
+      BQC_CUDA_TRY(cudaMemcpyAsync(&hinfo, svdinfo.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BQC_CUDA_TRY(cudaStreamSynchronize(s));
+      if (hinfo != 0) {
+        set_error("gesvd did not converge", __FILE__, __LINE__);
+        return BQC_E_CUDA;
+      }
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, no, no, no, &one, Uo.as<double>(),
+                               no, VTo.as<double>(), no, &zero, Ro.as<double>(), no));
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, no, no, &one, Cc.as<double>(),
+                               n, Ro.as<double>(), no, &zero, Ct.as<double>(), n));
+      k_procrustes_pair<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, Ca.as<double>(),
+                                                              Ct.as<double>(), Vp.as<double>(),
+                                                              Vm.as<double>());
+      BQC_LAUNCH_CHECK();
+      BQC_TRY(jk_k_rank2(df, Vp.as<double>(), Vm.as<double>(), K.as<double>(), s));
+      BQC_CUDA_TRY(cudaMemsetAsync(K2.p, 0, nn * 8, s));
+      BQC_CUDA_TRY(cudaMemcpyAsync(J.p, Jx.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+      BQC_CUDA_TRY(cudaMemsetAsync(J2.p, 0, nn * 8, s));
+      k_inc_fock<<<nblk(nn), 256, 0, s>>>(nn, Facc.as<double>(), J.as<double>(), J2.as<double>(),
+                                          K.as<double>(), K2.as<double>(), F.as<double>());
+      BQC_LAUNCH_CHECK();
+      return BQC_OK;
+    }
     BQC_TRY(eigh(w, ctx, t1.as<double>(), n, evd.as<double>(), work, info, s));
     hev.resize(n);
     BQC_CUDA_TRY(cudaMemcpyAsync(hev.data(), evd.p, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -374,6 +440,9 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
       // an anchor: the reference of the next increments
       BQC_CUDA_TRY(cudaMemcpyAsync(Facc.p, F.p, nn * 8, cudaMemcpyDeviceToDevice, s));
       BQC_CUDA_TRY(cudaMemcpyAsync(Dref.p, D.p, nn * 8, cudaMemcpyDeviceToDevice, s));
+      if (rank2)  // the anchor's occupied orbitals: the first nocc columns of Cc
+        BQC_CUDA_TRY(
+            cudaMemcpyAsync(Ca.p, Cc.p, (size_t)n * no * 8, cudaMemcpyDeviceToDevice, s));
     }
     k_axpby3<<<nblk(nn), 256, 0, s>>>(nn, H.as<double>(), 1.0, F.as<double>(), 1.0, nullptr, 0.0,
                                       t2.as<double>());

@@ -427,7 +427,10 @@ struct SyrkParams {
   int stages;
   double *part;  // [chunk][ntri][128][128]
   int *flag;
-  const MixScale *scale;  // KIND f16: partial tiles are unscaled by 1 / s_X^2
+  const MixScale *scale;  // KIND f16: partial tiles are unscaled by scale->k_unscale
+  // two-operand mode (3-D operands): tile (tm, tn) = sum X[tm] Y[tn]^T +
+  // Y[tm] X[tn]^T over the chunk, the lower tiles of a symmetric rank-2k update
+  int two;
   // blocked operand mode (direct mode): Y^T stored as [P block][i][mu][32];
   // rows mu, K = (i, P) with k-block kb = i * npb + P block; chunks are ranges
   // of kb_per_chunk k-blocks of kb_total
@@ -454,6 +457,7 @@ constexpr uint32_t kLoCol = 2 * kBM;             // TMEM columns of the compensa
 template <int KIND, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_syrk(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
+           const __grid_constant__ CUtensorMap mapYh, const __grid_constant__ CUtensorMap mapYl,
            const SyrkParams p) {
   using KD = Kind<KIND>;
   constexpr int KE = KD::kElems;
@@ -470,6 +474,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     prefetch_tmap(&mapXh);
     if (SPLIT == 3) prefetch_tmap(&mapXl);
+    if (p.two) {
+      prefetch_tmap(&mapYh);
+      prefetch_tmap(&mapYl);
+    }
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
@@ -494,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
       P0 = (int64_t)ch * p.p_per_chunk;
       nkb = max(0, min(p.naux, (int)P0 + p.p_per_chunk) - (int)P0) * p.nib;
+      if (p.two) nkb *= 2;  // first half X[tm] Y[tn], second half Y[tm] X[tn]
     }
   };
   if (warp == 0) {
@@ -522,12 +531,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_4d(a + 3 * kAStage, &mapXl, bar, 0, tn * kBM, ii, pb);
             }
           } else {
-            const int P = (int)P0 + kb / p.nib, i0 = (kb % p.nib) * KE;
-            tma_load_3d(a, &mapXh, bar, i0, tm * kBM, P);
-            tma_load_3d(a + kAStage, &mapXh, bar, i0, tn * kBM, P);
+            const int half = p.two ? nkb / 2 : nkb;
+            const bool second = kb >= half;
+            const int kk = second ? kb - half : kb;
+            const int P = (int)P0 + kk / p.nib, i0 = (kk % p.nib) * KE;
+            // one-operand: X[tm], X[tn]; two-operand: X[tm], Y[tn] then Y[tm], X[tn]
+            const CUtensorMap *mh = (p.two && second) ? &mapYh : &mapXh;
+            const CUtensorMap *ml = (p.two && second) ? &mapYl : &mapXl;
+            const CUtensorMap *nh = (p.two && !second) ? &mapYh : &mapXh;
+            const CUtensorMap *nl = (p.two && !second) ? &mapYl : &mapXl;
+            tma_load_3d(a, mh, bar, i0, tm * kBM, P);
+            tma_load_3d(a + kAStage, nh, bar, i0, tn * kBM, P);
             if (SPLIT == 3) {
-              tma_load_3d(a + 2 * kAStage, &mapXl, bar, i0, tm * kBM, P);
-              tma_load_3d(a + 3 * kAStage, &mapXl, bar, i0, tn * kBM, P);
+              tma_load_3d(a + 2 * kAStage, ml, bar, i0, tm * kBM, P);
+              tma_load_3d(a + 3 * kAStage, nl, bar, i0, tn * kBM, P);
             }
           }
         }
@@ -1330,7 +1347,7 @@ size_t mixed_workspace_bytes(int n, int naux, int nocc, int shadow) {
     b += (size_t)2 * naux * n * m.ldx * 2;                           // Xh16, Xl16
     b += (size_t)2 * m.ldx * m.ld16 * 2 + (size_t)n * m.ldx * 4;     // C split, Cf
     b += (size_t)(nocc + 1) * 4 + 256;                               // statistics, scales
-    b += (size_t)jpass_split((int64_t)n * (n + 1) / 2, naux) * n * (n + 1) / 2 * 8;  // J halves
+    b += (size_t)kJPieces * n * (n + 1) / 2 * 8;                   // J partials of the pieces
   } else {
     b += (size_t)2 * naux * n * m.ld * 4;                            // Bh, Bl
     b += (size_t)2 * naux * n * m.ldx * 4;                           // Xh, Xl
@@ -1346,11 +1363,15 @@ struct MixedState {
   DBuf Bl, Xl, Cl, Cf, wpart, w32;
   // FP16 split
   DBuf Bh16, Bl16, Xh16, Xl16, Ch16, Cl16, cstat, scale;
+  // second X operand of the two-operand (rank-2k) K build, allocated on first use
+  DBuf Yh16, Yl16, cstatB, scaleB, scaleK;
+  CUtensorMap mapYh, mapYl;
   int eB = 0;            // s_B = 2^eB
   double rownorm = 0.0;  // max_{P,mu} ||B_P,mu .||_2, unscaled, with a safety factor
   size_t bytes() const {
     return Bl.n + Xl.n + Cl.n + Cf.n + wpart.n + w32.n + Bh16.n + Bl16.n + Xh16.n + Xl16.n +
-           Ch16.n + Cl16.n + cstat.n + scale.n;
+           Ch16.n + Cl16.n + cstat.n + scale.n + Yh16.n + Yl16.n + cstatB.n + scaleB.n +
+           scaleK.n;
   }
 };
 
@@ -1424,6 +1445,7 @@ static int make_side_stream(Df *df, cudaStream_t s) {
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->join, cudaEventDisableTiming));
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->fork2, cudaEventDisableTiming));
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->prep, cudaEventDisableTiming));
+  for (auto &e : df->piece) BQC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   BQC_CUDA_TRY(cudaEventCreateWithFlags(&df->tjoin, cudaEventDisableTiming));
   return BQC_OK;
 }
@@ -1473,12 +1495,14 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   std::memcpy(&maxsq, &hb, 4);
   // |B row| <= |Bh row| / (1 - 2^-11); the factor also covers the float sums
   ms->rownorm = std::sqrt((double)maxsq) / (double)sB * (1.0 + 1.0 / 256.0);
-  {  // room for the J partials of the two halves
-    const int ph = naux / 2;
-    const size_t need = (size_t)std::max(jpass_split(df->npair, naux),
-                                         jpass_split(df->npair, std::max(1, ph)) +
-                                             jpass_split(df->npair, naux - ph)) *
-                        df->npair * 8;
+  {  // room for the J partials of the pieces
+    const int np = std::min(kJPieces, naux);
+    int slices = 0;
+    for (int k = 0; k < np; ++k)
+      slices += jpass_split(df->npair, (int)((int64_t)naux * (k + 1) / np) -
+                                           (int)((int64_t)naux * k / np));
+    const size_t need =
+        (size_t)std::max(jpass_split(df->npair, naux), slices) * df->npair * 8;
     if (df->Jp.n < need) BQC_TRY(df->Jp.alloc(ctx, need));
   }
   BQC_TRY(ms->Xh16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
@@ -1585,9 +1609,18 @@ int mixed_setup(Df *df, int shadow, cudaStream_t s) {
 // contraction w.
 static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_t s,
                        const CUtensorMap *Ah, const CUtensorMap *Al, int64_t rows, float *Xh,
-                       float *Xl, double *w_out, int P0 = 0, int P1 = -1, bool prep = true) {
-  // rows: all rows of the A operands; the launch covers aux functions [P0, P1)
+                       float *Xl, double *w_out, int P0 = 0, int P1 = -1, bool prep = true,
+                       __half *x16h = nullptr, __half *x16l = nullptr, float *cst = nullptr,
+                       MixScale *scl = nullptr) {
+  // rows: all rows of the A operands; the launch covers aux functions [P0, P1);
+  // FP16: X into (x16h, x16l) with statistics cst and scales scl when given
   MixedState *ms = df->mixed.get();
+  if (!x16h) {
+    x16h = ms->Xh16.as<__half>();
+    x16l = ms->Xl16.as<__half>();
+    cst = ms->cstat.as<float>();
+    scl = ms->scale.as<MixScale>();
+  }
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, no = b->nocc;
@@ -1596,15 +1629,14 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
   if (!prep) {
   } else if (kind == kKindF16) {
     const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld16, (int64_t)n * m.ldx);
-    BQC_CUDA_TRY(cudaMemsetAsync(ms->cstat.p, 0, ms->cstat.n, s));
-    k_cstats<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(C, n, no, ms->cstat.as<float>());
+    BQC_CUDA_TRY(cudaMemsetAsync(cst, 0, (size_t)(no + 1) * 4, s));
+    k_cstats<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(C, n, no, cst);
     BQC_LAUNCH_CHECK();
-    k_scales<<<1, 32, 0, s>>>(ms->cstat.as<float>(), no, ms->eB, ms->rownorm,
-                              ms->scale.as<MixScale>());
+    k_scales<<<1, 32, 0, s>>>(cst, no, ms->eB, ms->rownorm, scl);
     BQC_LAUNCH_CHECK();
     k_prep_c16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-        C, n, no, m.ld16, m.ldx, ms->scale.as<MixScale>(), ms->Ch16.as<__half>(),
-        ms->Cl16.as<__half>(), ms->Cf.as<float>());
+        C, n, no, m.ld16, m.ldx, scl, ms->Ch16.as<__half>(), ms->Cl16.as<__half>(),
+        ms->Cf.as<float>());
     BQC_LAUNCH_CHECK();
   } else {
     const int64_t tot = std::max<int64_t>((int64_t)m.ldx * m.ld, (int64_t)n * m.ldx);
@@ -1629,9 +1661,9 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
   p.tiles = (p.rows + kBM - 1) / kBM * m.ncg;
   p.Xh = Xh;
   p.Xl = Xl;
-  p.Xh16 = kind == kKindF16 ? ms->Xh16.as<__half>() : nullptr;
-  p.Xl16 = kind == kKindF16 ? ms->Xl16.as<__half>() : nullptr;
-  p.scale = kind == kKindF16 ? ms->scale.as<MixScale>() : nullptr;
+  p.Xh16 = kind == kKindF16 ? x16h : nullptr;
+  p.Xl16 = kind == kKindF16 ? x16l : nullptr;
+  p.scale = kind == kKindF16 ? scl : nullptr;
   p.Cf = ms->Cf.as<float>();
   p.wpart = ms->wpart.as<float>();
   p.flag = df->ctx->flag;
@@ -1651,7 +1683,8 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
 }
 
 static int mixed_syrk(Df *df, int kind, int split, const CUtensorMap *Xh, const CUtensorMap *Xl,
-                      int naux, double *K, cudaStream_t s) {
+                      int naux, double *K, cudaStream_t s, const CUtensorMap *Yh = nullptr,
+                      const CUtensorMap *Yl = nullptr, const MixScale *scl = nullptr) {
   MixedState *ms = df->mixed.get();
   const MixedPlan &m = ms->plan;
   const int n = df->basis->nbf;
@@ -1668,23 +1701,72 @@ static int mixed_syrk(Df *df, int kind, int split, const CUtensorMap *Xh, const 
   q.stages = m.sy_stages[k];
   q.part = df->Kpart.as<double>();
   q.flag = df->ctx->flag;
-  q.scale = kind == kKindF16 ? ms->scale.as<MixScale>() : nullptr;
+  q.scale = kind == kKindF16 ? (scl ? scl : ms->scale.as<MixScale>()) : nullptr;
   q.mode2d = 0;
   q.npb = 0;
   q.kb_total = 0;
   q.kb_per_chunk = 0;
+  q.two = Yh != nullptr;
+  if (q.two && kind != kKindF16) return BQC_E_UNSUPPORTED;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
   if (kind == kKindF16)
-    k_syrk<kKindF16, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
+    k_syrk<kKindF16, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, Yh ? *Yh : *Xh,
+                                                             Yl ? *Yl : *Xl, q);
   else if (split == 3)
-    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, q);
+    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(*Xh, *Xl, *Xh, *Xl, q);
   else
-    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(*Xh, *Xh, q);
+    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(*Xh, *Xh, *Xh, *Xh, q);
   BQC_LAUNCH_CHECK();
   k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(df->Kpart.as<double>(), q.nchunk,
                                                                   m.ntri, n, K);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
+}
+
+// k_unscale of a product of two differently scaled operands: 1 / (s_X s_Y),
+// the square root of the product of their 1 / s^2 (exact: powers of two).
+__global__ void k_scale_pair(const MixScale *a, const MixScale *b, MixScale *out) {
+  if (threadIdx.x != 0) return;
+  MixScale sc = *a;
+  sc.k_unscale = sqrt(a->k_unscale * b->k_unscale);
+  *out = sc;
+}
+
+// K = sum_P (W_P DY_P^T + DY_P W_P^T) with W_P = B_P Cw and DY_P = B_P Cd
+// (both N x nocc, row-major device inputs): the exchange matrix of the
+// symmetric density Cw Cd^T + Cd Cw^T, as two split-FP16 X passes and the
+// SYRK kernel in its two-operand mode.  The rounding error is relative to
+// |W||DY|, so a small Cd gives a small error (split-FP16 handles only).
+int jk_k_rank2(Df *df, const double *Cw, const double *Cd, double *K, cudaStream_t s) {
+  MixedState *ms = df->mixed.get();
+  if (!ms || ms->shadow != BQC_SHADOW_F16) return BQC_E_UNSUPPORTED;
+  const MixedPlan &m = ms->plan;
+  const Basis *b = df->basis;
+  const int n = b->nbf, naux = df->naux_loc;
+  const int64_t rows = (int64_t)naux * n;
+  Ctx *ctx = df->ctx;
+  if (!ms->Yh16.p) {
+    BQC_TRY(ms->Yh16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
+    BQC_TRY(ms->Yl16.alloc(ctx, (size_t)naux * n * m.ldx * 2));
+    BQC_TRY(ms->cstatB.alloc(ctx, (size_t)(b->nocc + 1) * 4));
+    BQC_TRY(ms->scaleB.alloc(ctx, sizeof(MixScale)));
+    BQC_TRY(ms->scaleK.alloc(ctx, sizeof(MixScale)));
+    const uint64_t dims[3] = {(uint64_t)m.ldx, (uint64_t)n, (uint64_t)naux};
+    const uint64_t str[2] = {(uint64_t)m.ldx * 2, (uint64_t)n * m.ldx * 2};
+    const uint32_t box[3] = {64, kBM, 1};
+    BQC_TRY(make_tmap_f16(&ms->mapYh, ms->Yh16.p, 3, dims, str, box));
+    BQC_TRY(make_tmap_f16(&ms->mapYl, ms->Yl16.p, 3, dims, str, box));
+  }
+  BQC_TRY(mixed_xpass(df, Cw, kKindF16, 3, s, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                      nullptr));
+  BQC_TRY(mixed_xpass(df, Cd, kKindF16, 3, s, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                      nullptr, 0, -1, true, ms->Yh16.as<__half>(), ms->Yl16.as<__half>(),
+                      ms->cstatB.as<float>(), ms->scaleB.as<MixScale>()));
+  k_scale_pair<<<1, 32, 0, s>>>(ms->scale.as<MixScale>(), ms->scaleB.as<MixScale>(),
+                                ms->scaleK.as<MixScale>());
+  BQC_LAUNCH_CHECK();
+  return mixed_syrk(df, kKindF16, 3, &ms->mapXh, &ms->mapXl, naux, K, s, &ms->mapYh, &ms->mapYl,
+                    ms->scaleK.as<MixScale>());
 }
 
 // w comes fused from the X pass in every mixed precision (FP32 row partials
@@ -1715,34 +1797,39 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
   const int64_t rows = (int64_t)naux * n;
   const bool j64 = split == 3 && df->B64.p;
   if (kind == kKindF16 && df->side && df->tcs && naux >= 2) {
-    // Two halves of the aux index on the tensor-core stream: X pass (h1),
-    // X pass (h2), SYRK, back to back; the J pass of each half follows it on
-    // the side stream, beside the next tensor-core kernel.
-    const int Ph = naux / 2;
+    // The X pass in kJPieces pieces of the aux index on the tensor-core
+    // stream, then the SYRK; the FP64 J pass of each piece follows it on the
+    // side stream, beside the next piece (the J stream needs about as long
+    // as the X pass and the SYRK together at the memory parallelism a J
+    // block gets beside a persistent tensor-core CTA, so it has to start
+    // early to end with them).
+    const int np = std::min(kJPieces, naux);
     cudaStream_t ts = df->tcs, js = df->side;
     df->mark(0, s);
     BQC_TRY(mixed_xpass(df, C, kind, split, s, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
                         nullptr, 0, 0, true));  // C split and scales only (no rows)
     BQC_CUDA_TRY(cudaEventRecord(df->prep, s));
     BQC_CUDA_TRY(cudaStreamWaitEvent(ts, df->prep, 0));
-    BQC_TRY(mixed_xpass(df, C, kind, split, ts, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
-                        df->w.as<double>(), 0, Ph, false));
-    if (df->timing && df->ev[6]) cudaEventRecord(df->ev[6], ts);
+    for (int k = 0; k < np; ++k) {
+      const int Pa = (int)((int64_t)naux * k / np), Pb = (int)((int64_t)naux * (k + 1) / np);
+      BQC_TRY(mixed_xpass(df, C, kind, split, ts, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                          df->w.as<double>(), Pa, Pb, false));
+      if (k == 0 && df->timing && df->ev[6]) cudaEventRecord(df->ev[6], ts);
+      BQC_CUDA_TRY(cudaEventRecord(df->piece[k], ts));
+    }
     df->j_from = 6;
-    BQC_CUDA_TRY(cudaEventRecord(df->fork, ts));
-    BQC_TRY(mixed_xpass(df, C, kind, split, ts, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
-                        df->w.as<double>(), Ph, naux, false));
     if (df->timing && df->ev[2]) cudaEventRecord(df->ev[2], ts);
-    BQC_CUDA_TRY(cudaEventRecord(df->fork2, ts));
     BQC_TRY(mixed_syrk(df, kind, split, &ms->mapXh, &ms->mapXl, naux, K, ts));
     if (df->timing && df->ev[3]) cudaEventRecord(df->ev[3], ts);
     BQC_CUDA_TRY(cudaEventRecord(df->tjoin, ts));
-    const int sp1 = jpass_split(df->npair, Ph);
-    BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork, 0));
-    BQC_TRY(jpass_fp64_range(df, 0, Ph, 0, js));
-    BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->fork2, 0));
-    BQC_TRY(jpass_fp64_range(df, Ph, naux, sp1, js));
-    BQC_TRY(jpass_unpack(df, sp1 + jpass_split(df->npair, naux - Ph), J, js));
+    int y = 0;
+    for (int k = 0; k < np; ++k) {
+      const int Pa = (int)((int64_t)naux * k / np), Pb = (int)((int64_t)naux * (k + 1) / np);
+      BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->piece[k], 0));
+      BQC_TRY(jpass_fp64_range(df, Pa, Pb, y, js));
+      y += jpass_split(df->npair, Pb - Pa);
+    }
+    BQC_TRY(jpass_unpack(df, y, J, js));
     if (df->timing && df->ev[5]) cudaEventRecord(df->ev[5], js);
     BQC_CUDA_TRY(cudaEventRecord(df->join, js));
     BQC_CUDA_TRY(cudaStreamWaitEvent(s, df->tjoin, 0));
@@ -2089,11 +2176,14 @@ int direct_mixed_finish(Df *df, int split, double *K, cudaStream_t s) {
   q.kb_total = dm->kb_total;
   q.kb_per_chunk = dm->sy_kbpc;
   q.scale = nullptr;
+  q.two = 0;
   const int grid = std::min(m.grid, q.ntri * q.nchunk);
   if (split == 3)
-    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(dm->mapYh, dm->mapYl, q);
+    k_syrk<kKindTF32, 3><<<grid, kThreads, m.sy_smem[1], s>>>(dm->mapYh, dm->mapYl, dm->mapYh,
+                                                             dm->mapYl, q);
   else
-    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(dm->mapYh, dm->mapYh, q);
+    k_syrk<kKindTF32, 1><<<grid, kThreads, m.sy_smem[0], s>>>(dm->mapYh, dm->mapYh, dm->mapYh,
+                                                             dm->mapYh, q);
   BQC_LAUNCH_CHECK();
   k_syrk_reduce<<<dim3((unsigned)m.ntri, kBM / 32), 256, 0, s>>>(dm->Kpart.as<double>(),
                                                                   q.nchunk, m.ntri, n, K);
