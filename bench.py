@@ -256,13 +256,15 @@ def config(mol, prec):
 
 
 def serve_leg(bqc, ctx, workload, nreq, rate, slots=8, prec=None, incremental=True,
-              policy=0, budget=150 * 10 ** 9, log=None):
+              policy=0, budget=150 * 10 ** 9, log=None, grouped=False):
     """Submits the first `nreq` requests of the seed-2025 Poisson stream at
     their arrival times (offered `rate` req/s) to one server and waits for
-    all; latency = completion - arrival (the server's submit time)."""
+    all; latency = completion - arrival (the server's submit time).  With
+    grouped, the mixed-stage Fock builds of the solves in flight run as
+    grouped launches."""
     stream = workload.serving_stream(nreq=nreq, rate_hz=rate)
     srv = bqc.Server(ctx, max_slots=slots, hbm_budget=budget, prec=prec, policy=policy,
-                     incremental=incremental)
+                     incremental=incremental, grouped=grouped)
     t0 = time.perf_counter()
     tickets = []
     for (ta, n, rid) in stream:
@@ -284,13 +286,17 @@ def serve_leg(bqc, ctx, workload, nreq, rate, slots=8, prec=None, incremental=Tr
                               f"run={r['t_done'] - r['t_admit']:.2f}s", file=log, flush=True)
         time.sleep(0.02)
     wall = time.perf_counter() - t0
+    gst = srv.group_stats()
     srv.close()
     lat = sorted(done[t]["t_done"] - done[t]["t_submit"] for (_, _, t) in tickets)
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
-    return {"offered_req_per_s": rate, "requests": len(lat), "p50_ms": q(0.5) * 1e3,
-            "p99_ms": q(0.99) * 1e3, "solves_per_s": len(lat) / wall, "wall_s": wall,
-            "converged": sum(1 for t in done.values() if t["status"] == 0),
-            "sizes_n": [n for (_, n, _) in tickets]}
+    out = {"offered_req_per_s": rate, "requests": len(lat), "p50_ms": q(0.5) * 1e3,
+           "p99_ms": q(0.99) * 1e3, "solves_per_s": len(lat) / wall, "wall_s": wall,
+           "converged": sum(1 for t in done.values() if t["status"] == 0),
+           "sizes_n": [n for (_, n, _) in tickets]}
+    if grouped:
+        out["grouped"] = gst
+    return out
 
 
 def run_serve(args):
@@ -564,9 +570,12 @@ def run_mp2(args):
     e2 = bqc.mp2(df, C, eps, prec=mp)
     dt = time.perf_counter() - t0
     clk = clocks.stop()
-    e2_64 = None
+    e2_64, dt64 = None, None
     if mp != bqc.PREC_FP64 and nw <= 32:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         e2_64 = bqc.mp2(df, C, eps, prec=bqc.PREC_FP64)
+        dt64 = time.perf_counter() - t1
     n, naux, no = basis.nbf, basis.naux, basis.nocc
     nv = r["nmo"] - no
     bi = max(1, min(16, no, int((1 << 27) ** 0.5 / max(1, nv))))
@@ -599,7 +608,7 @@ def run_mp2(args):
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": args.mp2_prec,
             "config": {"workload": f"{mol.name} DF-MP2 after the staged SCF, N={n}, Naux={naux}, "
                                    f"nocc={no}, nvir={nv}"},
-            "e2_Eh": e2, "e2_fp64_Eh": e2_64,
+            "e2_Eh": e2, "e2_fp64_Eh": e2_64, "fp64_s": dt64,
             "e_scf_Eh": r["energy"], "roofline": roof, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -829,6 +838,12 @@ def main():
         for rate in (args.serve_rate, args.serve_low_rate):
             sv[f"{rate:g}_req_per_s"] = serve_leg(bqc, ctx, workload, args.serve_leg, rate,
                                                   prec=MIX, log=sys.stderr)
+        if MIX == bqc.PREC_MIXED_F16X3:
+            # the same offered load with the mixed-stage builds of the solves
+            # in flight batched into grouped launches
+            sv[f"{args.serve_rate:g}_req_per_s_grouped"] = serve_leg(
+                bqc, ctx, workload, args.serve_leg, args.serve_rate, prec=MIX, log=sys.stderr,
+                grouped=True)
         line["serve"] = {"prec": args.prec + " staged, incremental FP64 stage", "slots": 8,
                          "hbm_budget_gb": 150, "policy": "backfill",
                          "workload": f"first {args.serve_leg} requests of the seed-2025 Poisson "

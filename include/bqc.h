@@ -257,6 +257,21 @@ int bqc_jk_fp64_noalloc(const double *B_dev, int naux, int nbf, const double *C_
 int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, double *K,
                 bqc_stream_t stream);
 
+/* Grouped split-FP16 Fock builds of n independent molecules (the batching
+ * of launch-bound small kernels of Sec. 2.4.2 applied to Sec. 2.2's two
+ * passes): J[k], K[k] of dfs[k] with C_dev[k] (device, row-major N_k x
+ * nocc_k, as bqc_jk), all at MIXED_F16X3.  Every handle must be stored mode,
+ * unsharded and built with BQC_SHADOW_F16 (else BQC_E_UNSUPPORTED), on one
+ * device, and appear once.  The X passes of all molecules run as one
+ * persistent tensor-core launch, then their FP64 J passes as one launch and
+ * their SYRKs as one launch (up to 12 molecules per launch; more are taken
+ * twelve at a time), each molecule keeping its own plan, so J[k] and K[k]
+ * equal bqc_jk's K exactly and its J to the rounding of the J pass's aux
+ * chunking.  Uses each handle's own workspace: no handle may have another
+ * build in flight.  Async on `stream`. */
+int bqc_jk_grouped(int n, bqc_df *const *dfs, const double *const *C_dev, double *const *J,
+                   double *const *K, bqc_stream_t stream);
+
 /* Per-phase device timing of bqc_jk (a profiling aid).  enable != 0 makes
  * every following bqc_jk on this handle record CUDA events at its phase
  * boundaries on its stream (leave it off while capturing a graph).
@@ -400,6 +415,12 @@ typedef struct {
   bqc_scf_opts scf;    /* SCF options for every request                       */
   int policy;          /* bqc_serve_policy                                    */
   int max_skips;       /* backfill starvation bound (<= 0: 8)                 */
+  /* != 0 (prec MIXED_F16X3 only): the mixed-stage Fock builds of the solves
+   * in flight are batched into grouped launches (bqc_jk_grouped); the first
+   * solve to hand in a build waits at most group_window_us (<= 0: 1000) for
+   * the other solves of the mixed stage before the batch launches. */
+  int grouped;
+  double group_window_us;
 } bqc_serve_opts;
 
 typedef struct {
@@ -438,6 +459,9 @@ int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res);
  * requests are done; BQC_E_TIMEOUT otherwise. */
 int bqc_serve_drain(bqc_server *srv, double timeout_s);
 int bqc_serve_destroy(bqc_server *srv);
+/* Grouped-build counters of a server created with grouped != 0: batches
+ * launched, builds they held, and the largest batch (all 0 otherwise). */
+int bqc_serve_group_stats(bqc_server *srv, uint64_t *batches, uint64_t *builds, int *max_batch);
 /* Predicted device bytes of a request of this size solved with `prec` (the
  * admission ledger); 0 for an invalid argument. */
 size_t bqc_serve_footprint(int nbf, int naux, int nocc, int prec);

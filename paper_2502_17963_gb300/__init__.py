@@ -20,8 +20,10 @@ from typing import Optional, Tuple
 from . import _build
 
 BQC_OK = 0
+BQC_E_INVALID = -1
 BQC_E_NOT_CONVERGED = -4
 BQC_E_NOT_READY = -8
+BQC_E_UNSUPPORTED = -9
 PREC_FP64 = 0
 PREC_MIXED_TF32 = 1
 PREC_MIXED_TF32X3 = 2
@@ -74,7 +76,8 @@ class bqc_scf_result(ctypes.Structure):
 class bqc_serve_opts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("prec", ctypes.c_int), ("scf", bqc_scf_opts), ("policy", ctypes.c_int),
-                ("max_skips", ctypes.c_int)]
+                ("max_skips", ctypes.c_int), ("grouped", ctypes.c_int),
+                ("group_window_us", ctypes.c_double)]
 
 
 class bqc_request(ctypes.Structure):
@@ -135,6 +138,10 @@ _SIGS = {
     "bqc_serve_drain": (ip, [vp, dp]),
     "bqc_serve_destroy": (ip, [vp]),
     "bqc_serve_footprint": (ctypes.c_size_t, [ip, ip, ip, ip]),
+    "bqc_serve_group_stats": (ip, [vp, ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int)]),
+    "bqc_jk_grouped": (ip, [ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                            ctypes.POINTER(vp), vp]),
     "bqc_wait_selftest": (ip, [vp, ctypes.c_longlong, vp]),
     "bqc_mp2": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
 }
@@ -461,12 +468,13 @@ class Server:
                  prec: int = PREC_MIXED_TF32X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
                  stage_tol: float = 1e-5, max_iter: int = 100, diis_space: int = 8,
                  orth_thresh: float = 1e-8, policy: int = 0, max_skips: int = 8,
-                 incremental: bool = False):
+                 incremental: bool = False, grouped: bool = False,
+                 group_window_us: float = 1000.0):
         self.ctx = ctx
         o = bqc_serve_opts(max_slots, hbm_budget, prec,
                            bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space,
                                         prec, orth_thresh, 1 if incremental else 0),
-                           policy, max_skips)
+                           policy, max_skips, 1 if grouped else 0, group_window_us)
         h = vp()
         check(lib().bqc_serve_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "bqc_serve_create")
         self.h = h
@@ -493,6 +501,13 @@ class Server:
     def drain(self, timeout_s: float = 0.0):
         check(lib().bqc_serve_drain(self.h, timeout_s), "bqc_serve_drain")
 
+    def group_stats(self):
+        """Grouped-build counters: batches, builds, largest batch."""
+        b, j, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+        check(lib().bqc_serve_group_stats(self.h, ctypes.byref(b), ctypes.byref(j),
+                                          ctypes.byref(m)), "bqc_serve_group_stats")
+        return dict(batches=b.value, builds=j.value, max_batch=m.value)
+
     def close(self):
         if getattr(self, "h", None):
             lib().bqc_serve_destroy(self.h)
@@ -503,6 +518,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def jk_grouped(dfs, Cs, Js=None, Ks=None, stream=None):
+    """bqc_jk_grouped: split-FP16 J, K of several independent handles in
+    grouped launches; returns the lists (Js, Ks) of N_k x N_k device tensors."""
+    n = len(dfs)
+    if len(Cs) != n:
+        raise ValueError("one C per handle")
+    Js = [_empty((d.basis.nbf, d.basis.nbf)) for d in dfs] if Js is None else Js
+    Ks = [_empty((d.basis.nbf, d.basis.nbf)) for d in dfs] if Ks is None else Ks
+    arr = ctypes.c_void_p * max(1, n)
+    h = arr(*[d.h for d in dfs])
+    c = arr(*[_ptr(x) for x in Cs])
+    j = arr(*[_ptr(x) for x in Js])
+    k = arr(*[_ptr(x) for x in Ks])
+    check(lib().bqc_jk_grouped(n, h, c, j, k, _stream_ptr(stream)), "bqc_jk_grouped")
+    return Js, Ks
 
 
 def serve_footprint(nbf: int, naux: int, nocc: int, prec: int = PREC_MIXED_TF32X3) -> int:

@@ -39,19 +39,12 @@ __global__ void __launch_bounds__(256) k_wdot(const double *X, const double *C, 
   if (threadIdx.x == 0) w[P] = red[0];
 }
 
-// J pass over packed FP64 B: Jp[y][col] = sum_{P in chunk y} w_P B[P][col];
-// each thread owns two adjacent columns and streams the chunk's P (one read
-// of B, coalesced), eight 16-byte loads in flight per thread, P in
-// increasing order.  gridDim.y aux chunks give small systems enough blocks;
-// the chunk partials are summed in a fixed order by k_unpack_jsum.
-__global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
-                                                 const double *__restrict__ w, int naux,
-                                                 int64_t npair, double *__restrict__ Jp) {
-  const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
-  if (c2 >= npair) return;
-  const int per = (naux + gridDim.y - 1) / gridDim.y;
-  const int Pa = blockIdx.y * per, Pb = min(naux, Pa + per);
-  double *out = Jp + (int64_t)blockIdx.y * npair;
+// J pass over packed FP64 B: out[col] = sum_{P in [Pa, Pb)} w_P B[P][col] for
+// the two adjacent columns c2, c2 + 1 a thread owns; P streams in increasing
+// order (one read of B, coalesced), eight 16-byte loads in flight per thread.
+__device__ __forceinline__ void jpass64_cols(const double *__restrict__ B,
+                                             const double *__restrict__ w, int Pa, int Pb,
+                                             int64_t npair, int64_t c2, double *__restrict__ out) {
   double a0 = 0.0, a1 = 0.0;
   if (c2 + 1 < npair && (npair % 2 == 0)) {
     const double2 *b2 = reinterpret_cast<const double2 *>(B + c2);
@@ -87,9 +80,21 @@ __global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
   }
 }
 
-// J pass over packed FP64 B for aux functions [P0, P1), partials into the
-// slices y0 .. y0 + gridDim.y - 1 (the two-half pipeline of the split-FP16
-// build); the same streaming scheme as k_jpass64.
+// Jp[y][col] = sum_{P in chunk y} w_P B[P][col]: gridDim.y aux chunks give
+// small systems enough blocks; the chunk partials are summed in a fixed order
+// by k_unpack_jsum.
+__global__ void __launch_bounds__(256) k_jpass64(const double *__restrict__ B,
+                                                 const double *__restrict__ w, int naux,
+                                                 int64_t npair, double *__restrict__ Jp) {
+  const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (c2 >= npair) return;
+  const int per = (naux + gridDim.y - 1) / gridDim.y;
+  const int Pa = blockIdx.y * per, Pb = min(naux, Pa + per);
+  jpass64_cols(B, w, Pa, Pb, npair, c2, Jp + (int64_t)blockIdx.y * npair);
+}
+
+// The same for aux functions [P0, P1), partials into the slices y0 .. y0 +
+// gridDim.y - 1 (the pieces of the split-FP16 build's pipeline).
 __global__ void __launch_bounds__(256) k_jpass64_range(const double *__restrict__ B,
                                                        const double *__restrict__ w, int P0,
                                                        int P1, int64_t npair, int y0,
@@ -98,45 +103,37 @@ __global__ void __launch_bounds__(256) k_jpass64_range(const double *__restrict_
   if (c2 >= npair) return;
   const int per = (P1 - P0 + gridDim.y - 1) / gridDim.y;
   const int Pa = P0 + blockIdx.y * per, Pb = min(P1, Pa + per);
-  double *out = Jp + (int64_t)(y0 + blockIdx.y) * npair;
-  double a0 = 0.0, a1 = 0.0;
-  if (c2 + 1 < npair && (npair % 2 == 0)) {
-    const double2 *b2 = reinterpret_cast<const double2 *>(B + c2);
-    const int64_t st = npair / 2;
-    int P = Pa;
-    for (; P + 8 <= Pb; P += 8) {
-      double2 v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = __ldg(b2 + (int64_t)(P + k) * st);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const double wp = __ldg(w + P + k);
-        a0 = fma(wp, v[k].x, a0);
-        a1 = fma(wp, v[k].y, a1);
-      }
-    }
-    for (; P < Pb; ++P) {
-      const double2 v = __ldg(b2 + (int64_t)P * st);
-      const double wp = __ldg(w + P);
-      a0 = fma(wp, v.x, a0);
-      a1 = fma(wp, v.y, a1);
-    }
-    out[c2] = a0;
-    out[c2 + 1] = a1;
-  } else {
-    for (int P = Pa; P < Pb; ++P) {
-      const double wp = __ldg(w + P);
-      a0 = fma(wp, B[(int64_t)P * npair + c2], a0);
-      if (c2 + 1 < npair) a1 = fma(wp, B[(int64_t)P * npair + c2 + 1], a1);
-    }
-    out[c2] = a0;
-    if (c2 + 1 < npair) out[c2 + 1] = a1;
-  }
+  jpass64_cols(B, w, Pa, Pb, npair, c2, Jp + (int64_t)(y0 + blockIdx.y) * npair);
 }
 
-// J[r][c] = sum_y Jp[y][pair(r, c)] (full symmetric N x N, chunks in order).
-__global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n, double *J) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Grouped J pass of independent problems in one launch: problem k owns the
+// blocks [off[k], off[k + 1]) as xb[k] column blocks times sp[k] aux chunks.
+struct JGroup {
+  const double *B[kMaxGroup];
+  const double *w[kMaxGroup];
+  double *Jp[kMaxGroup];
+  double *J[kMaxGroup];
+  int64_t npair[kMaxGroup];
+  int naux[kMaxGroup], sp[kMaxGroup], xb[kMaxGroup], n[kMaxGroup];
+  int off[kMaxGroup + 1];
+  int nprob;
+};
+
+__global__ void __launch_bounds__(256) k_jpass64_grp(const __grid_constant__ JGroup g) {
+  const int bid = blockIdx.x;
+  int k = 0;
+  while (k + 1 < g.nprob && bid >= g.off[k + 1]) ++k;
+  const int lb = bid - g.off[k], y = lb / g.xb[k], xb = lb % g.xb[k];
+  const int64_t npair = g.npair[k];
+  const int64_t c2 = ((int64_t)xb * blockDim.x + threadIdx.x) * 2;
+  if (c2 >= npair) return;
+  const int per = (g.naux[k] + g.sp[k] - 1) / g.sp[k];
+  const int Pa = y * per, Pb = min(g.naux[k], Pa + per);
+  jpass64_cols(g.B[k], g.w[k], Pa, Pb, npair, c2, g.Jp[k] + (int64_t)y * npair);
+}
+
+__device__ __forceinline__ void unpack_jsum_one(const double *Jp, int nsplit, int64_t npair, int n,
+                                                double *J, int64_t i) {
   if (i >= (int64_t)n * n) return;
   const int64_t r = i / n, c = i % n;
   const int64_t hi = r > c ? r : c, lo = r > c ? c : r;
@@ -144,6 +141,16 @@ __global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n
   double s = Jp[q];
   for (int y = 1; y < nsplit; ++y) s += Jp[(int64_t)y * npair + q];
   J[i] = s;
+}
+
+__global__ void k_unpack_jsum(const double *Jp, int nsplit, int64_t npair, int n, double *J) {
+  unpack_jsum_one(Jp, nsplit, npair, n, J, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_unpack_jsum_grp(const __grid_constant__ JGroup g) {
+  const int k = blockIdx.y;
+  unpack_jsum_one(g.Jp[k], g.sp[k], g.npair[k], g.n[k], g.J[k],
+                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // aux chunks of the J pass: enough blocks for four per SM, at least 64 P each
@@ -233,6 +240,41 @@ int jpass_unpack(Df *df, int nslice, double *J, cudaStream_t s) {
   const int n = df->basis->nbf;
   k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(),
                                                                          nslice, df->npair, n, J);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int group_jpass(Df *const *dfs, double *const *J, int n, cudaStream_t s) {
+  if (n <= 0 || n > kMaxGroup) return BQC_E_INVALID;
+  JGroup g;
+  std::memset(&g, 0, sizeof(g));
+  int blocks = 0;
+  int64_t nn_max = 0;
+  for (int k = 0; k < n; ++k) {
+    Df *df = dfs[k];
+    if (!df->B64.p) return BQC_E_INVALID;
+    const int64_t npair = df->npair;
+    const int naux = df->naux_loc, nb = df->basis->nbf;
+    const int sp = jpass_split(npair, naux);
+    if (df->Jp.n < (size_t)sp * npair * 8) return BQC_E_INVALID;
+    g.B[k] = df->B64.as<double>();
+    g.w[k] = df->w.as<double>();
+    g.Jp[k] = df->Jp.as<double>();
+    g.J[k] = J[k];
+    g.npair[k] = npair;
+    g.naux[k] = naux;
+    g.sp[k] = sp;
+    g.xb[k] = (int)((npair / 2 + 256) / 256);
+    g.n[k] = nb;
+    g.off[k] = blocks;
+    blocks += g.xb[k] * sp;
+    nn_max = std::max(nn_max, (int64_t)nb * nb);
+  }
+  g.off[n] = blocks;
+  g.nprob = n;
+  k_jpass64_grp<<<(unsigned)blocks, 256, 0, s>>>(g);
+  BQC_LAUNCH_CHECK();
+  k_unpack_jsum_grp<<<dim3((unsigned)((nn_max + 255) / 256), (unsigned)n), 256, 0, s>>>(g);
   BQC_LAUNCH_CHECK();
   return BQC_OK;
 }

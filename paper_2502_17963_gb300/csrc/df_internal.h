@@ -8,6 +8,9 @@ namespace bqc {
 
 // Aux pieces of the split-FP16 build's X pass (each followed by its J pass).
 constexpr int kJPieces = 4;
+// Problems of one grouped launch (the problem table is a kernel parameter).
+constexpr int kMaxGroup = 12;
+struct FockGroup;
 
 struct MixedState;
 size_t mixed_bytes(const MixedState *ms);
@@ -71,7 +74,13 @@ struct Df {
   cudaStream_t tcs = nullptr;  // tensor-core stream, one priority level above side
   cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, prep = nullptr, tjoin = nullptr;
   cudaEvent_t piece[kJPieces] = {};  // end of each X-pass piece (split-FP16 pipeline)
+  // grouped builds (serving): the group this handle's mixed builds join, and
+  // the events that hand a build to the group and back
+  FockGroup *group = nullptr;
+  cudaEvent_t gready = nullptr, gdone = nullptr;
   ~Df() {
+    if (gready) cudaEventDestroy(gready);
+    if (gdone) cudaEventDestroy(gdone);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
@@ -131,6 +140,26 @@ int mp2_tc_setup(Ctx *ctx, const double *Bt, int naux, int nocc, int nv, int *fl
 int mp2_tc_block(Mp2Tc *m, int nv, int i0, int ni, int j0, int nj, double *V, int64_t ldv,
                  int *flag, cudaStream_t s);
 int jk4c_setup(Df *df, cudaStream_t s);
+// Grouped split-FP16 builds of independent handles (stored, unsharded, FP16
+// shadows): group_prep splits one handle's C (its own stream); group_xpass
+// (X and w), group_jpass (FP64 J) and group_syrk (K) then each run n <=
+// kMaxGroup problems in one launch (plus one small reduction launch).
+int group_prep(Df *df, const double *C, cudaStream_t s);
+int group_xpass(Df *const *dfs, int n, cudaStream_t s);
+int group_jpass(Df *const *dfs, double *const *J, int n, cudaStream_t s);
+int group_syrk(Df *const *dfs, double *const *K, int n, cudaStream_t s);
+// All three for n handles whose C was split by group_prep, on stream s.
+int group_build(Df *const *dfs, double *const *J, double *const *K, int n, cudaStream_t s);
+// A mixed build of one handle through its group (blocks until the group has
+// launched it; the build is complete in stream order on s on return).
+int jk_grouped(Df *df, const double *C, double *J, double *K, cudaStream_t s);
+void group_enter(FockGroup *g);
+void group_leave(FockGroup *g);
+// A group whose batches launch on a new stream of the given priority; window_s
+// bounds how long a leader waits for the registered solves.
+FockGroup *group_create(double window_s, int max_jobs, int priority, int *status);
+void group_destroy(FockGroup *g);
+void group_stats(FockGroup *g, uint64_t *batches, uint64_t *jobs, int *max_batch);
 int jk_4c(Df *df, const double *C, int prec, double *J, double *K, cudaStream_t s);
 
 }  // namespace bqc

@@ -258,6 +258,20 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   std::vector<int> slot;  // DIIS entries in age order (slot indices)
   std::vector<double> Bm; // Gram matrix of errors in age order
   int stage = o.prec;
+  // a solve whose mixed builds join a group (serving) is counted there while
+  // it is in the mixed stage, so a batch leader knows whom to wait for
+  struct GroupSeat {
+    FockGroup *g = nullptr;
+    void release() {
+      if (g) group_leave(g);
+      g = nullptr;
+    }
+    ~GroupSeat() { release(); }
+  } seat;
+  if (df->group && stage == BQC_PREC_MIXED_F16X3) {
+    seat.g = df->group;
+    group_enter(seat.g);
+  }
   int mixed_iters = 0, since_best = 0;
   double best = INFINITY;
   double E = 0.0, Eprev = 0.0, emax = INFINITY;
@@ -277,6 +291,8 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2, &Jx}) BQC_TRY(p->alloc(ctx, nn * 8));
     BQC_TRY(evd.alloc(ctx, (size_t)n * 8));
     BQC_TRY(D2p.alloc(ctx, (size_t)n * (n + 1) / 2 * 8));
+    BQC_TRY(Vp.alloc(ctx, (size_t)n * no * 8));
+    BQC_TRY(Vm.alloc(ctx, (size_t)n * no * 8));
   }
   if (rank2) {
     const size_t on = (size_t)n * no * 8, oo = (size_t)no * no * 8;
@@ -286,8 +302,6 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     BQC_SOLVER_TRY(cusolverDnDgesvd_bufferSize(w.sol, no, no, &svd_lwork));
     BQC_TRY(svdw.alloc(ctx, (size_t)std::max(1, svd_lwork) * 8));
     BQC_TRY(svdinfo.alloc(ctx, sizeof(int)));
-    BQC_TRY(Vp.alloc(ctx, (size_t)n * no * 8));
-    BQC_TRY(Vm.alloc(ctx, (size_t)n * no * 8));
   }
   bool need_anchor = true;    // the first FP64-stage build is full
   bool last_incremental = false;
@@ -406,7 +420,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
       BQC_TRY(incremental_build());
       ++res->builds_incremental;
       ++inc_since_anchor;
-    } else if (use_graph && stage >= 0 && stage < 4) {
+    } else if (use_graph && stage >= 0 && stage < 4 && !(df->group && stage != BQC_PREC_FP64)) {
       if (!gexec[stage]) {
         cudaGraph_t graph = nullptr;
         BQC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -534,6 +548,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
         res->switch_rule = emax < o.stage_tol ? BQC_SWITCH_STAGE_TOL : BQC_SWITCH_FLOOR;
         res->switch_err = emax;
         stage = BQC_PREC_FP64;
+        seat.release();
         slot.clear();
         Bm.clear();
         have_prev = false;

@@ -156,6 +156,7 @@ struct bqc_server {
   bool stop = false;
   int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range
   uint64_t releases = 0;                  // solves finished (their memory freed)
+  bqc::FockGroup *group = nullptr;        // grouped mixed-stage builds (opts.grouped)
   std::chrono::steady_clock::time_point t0;
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -207,6 +208,7 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
     o.hbm_limit = 0;
     st = bqc_df_build(srv->ctx, basis, &o, (bqc_stream_t)s, &df);
   }
+  if (st == BQC_OK && srv->group) df->group = srv->group;
   if (st == BQC_OK) {
     bqc_scf_opts so = srv->opts.scf;
     so.prec = srv->opts.prec;
@@ -364,6 +366,12 @@ int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out)
   bqc_ctx *ic = nullptr;
   BQC_TRY(bqc_ctx_create(ctx->device, budget, arena_alloc, arena_free, &srv->arena, &ic));
   srv->ctx = ic;
+  if (o.grouped && o.prec == BQC_PREC_MIXED_F16X3) {
+    int gst = BQC_OK;
+    const double win = o.group_window_us > 0.0 ? o.group_window_us * 1e-6 : 1e-3;
+    srv->group = group_create(win, o.max_slots, srv->prio_greatest, &gst);
+    if (!srv->group) return gst;
+  }
   srv->t0 = std::chrono::steady_clock::now();
   for (int i = 0; i < o.max_slots; ++i) srv->workers.emplace_back(worker_main, srv.get());
   *out = srv.release();
@@ -444,8 +452,15 @@ int bqc_serve_destroy(bqc_server *srv) {
   }
   srv->cv_work.notify_all();
   for (auto &t : srv->workers) t.join();
+  group_destroy(srv->group);
   if (srv->ctx) bqc_ctx_destroy(srv->ctx);
   delete srv;
+  return BQC_OK;
+}
+
+int bqc_serve_group_stats(bqc_server *srv, uint64_t *batches, uint64_t *builds, int *max_batch) {
+  if (!srv || !batches || !builds || !max_batch) return BQC_E_INVALID;
+  group_stats(srv->group, batches, builds, max_batch);
   return BQC_OK;
 }
 

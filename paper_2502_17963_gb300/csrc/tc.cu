@@ -169,15 +169,42 @@ struct XpassParams {
   int64_t xrows;
 };
 
+// Whether the X pass keeps its chain sums in TMEM (two accumulator buffers
+// and the running sum, 3 XN columns, fit in the 512 columns of an SM).
+__host__ __device__ constexpr bool xpass_acc_tmem(int XN) { return 3 * XN <= 512; }
+// Resident CTAs the register budget is sized for: 2 leaves room for other
+// kernels' blocks (the J pass) beside a persistent CTA that needs few
+// registers.
+__host__ __device__ constexpr int xpass_min_blocks(int XN) { return xpass_acc_tmem(XN) ? 2 : 1; }
+
+// One X-pass tile as the kernel body sees it: the operand maps, the
+// parameters of its problem, its first row, column group and width (xn <= the
+// kernel's XN; one problem per launch has xn = XN, a grouped launch takes the
+// width of each problem's own plan).
+struct XTile {
+  const CUtensorMap *Ah, *Al, *Ch, *Cl;
+  const XpassParams *p;
+  int64_t m0;
+  int cg, xn;
+};
+
+// Tile locator of a single-problem launch.
+template <int XN> struct XLocOne {
+  const CUtensorMap *Ah, *Al, *Ch, *Cl;
+  const XpassParams *p;
+  __device__ __forceinline__ XTile at(int64_t t) const {
+    return XTile{Ah, Al, Ch, Cl, p, p->row0 + (t / p->ncg) * kBM, (int)(t % p->ncg), XN};
+  }
+};
+
 // Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
 // t / ncg, column group t % ncg), so neighbouring CTAs share A rows in L2.
 // EPI 0: X[row][i] (hi/lo) and the fused w_P partials; EPI 1: X^T layout
 // (TF32 only).  KIND: TF32 or FP16 operands (k-blocks of 32 or 64 elements).
-template <int KIND, int XN, int SPLIT, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_xpass(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
-            const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
-            const XpassParams p) {
+// LOC maps a tile index to its problem (one problem, or a grouped table).
+template <int KIND, int XN, int SPLIT, int EPI, class LOC>
+__device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int stages,
+                                           int *flag) {
   static_assert(KIND == kKindTF32 || EPI == 0, "the transposed epilogue is TF32 only");
   using KD = Kind<KIND>;
   constexpr int KE = KD::kElems;
@@ -185,23 +212,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int NS = SPLIT == 3 ? 2 : 1;  // operand parts per side
   constexpr uint32_t a_bytes = kAStage, c_bytes = XN * 128;
   constexpr uint32_t stage_bytes = NS * (a_bytes + c_bytes);
-  constexpr int TCOLS = (2 * XN <= 32) ? 32 : (2 * XN <= 64) ? 64 : (2 * XN <= 128) ? 128
-                                            : (2 * XN <= 256) ? 256 : 512;
+  // ACC_T: the running sum of the chains lives in a third TMEM region
+  // (columns 2 XN .. 3 XN) instead of registers, so the epilogue needs few
+  // registers and other kernels' blocks fit beside the persistent CTA
+  constexpr bool ACC_T = xpass_acc_tmem(XN);
+  constexpr int UCOLS = ACC_T ? 3 * XN : 2 * XN;
+  constexpr int TCOLS = (UCOLS <= 32) ? 32 : (UCOLS <= 64) ? 64 : (UCOLS <= 128) ? 128
+                                            : (UCOLS <= 256) ? 256 : 512;
+  constexpr int AREG = ACC_T ? 1 : HALF;  // register accumulators per thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
-  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * stages;
+  const uint32_t tfull0 = full0 + 16 * stages, tempty0 = tfull0 + 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    prefetch_tmap(&mapAh);
-    prefetch_tmap(&mapCh);
-    if (SPLIT == 3) {
-      prefetch_tmap(&mapAl);
-      prefetch_tmap(&mapCl);
-    }
-    for (int s = 0; s < p.stages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -216,44 +243,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t sbase = smem_u32(smem);
-  const int ngroups = (p.kblocks + kGroupKb - 1) / kGroupKb;
   bool ok = true;
   if (warp == 0) {
     if (lane == 0) {
       int64_t kg = 0;  // k-blocks issued by this CTA
-      for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
-        const int64_t m0 = p.row0 + (t / p.ncg) * kBM;
-        const int c0 = (int)(t % p.ncg) * XN;
-        for (int kb = 0; kb < p.kblocks && ok; ++kb, ++kg) {
-          const int s = (int)(kg % p.stages);
-          if (kg >= p.stages)
-            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 11);
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const XTile T = loc.at(t);
+        const int kblocks = T.p->kblocks;
+        const int c0 = T.cg * T.xn;
+        const uint32_t tx = (uint32_t)NS * (a_bytes + (uint32_t)T.xn * 128);
+        for (int kb = 0; kb < kblocks && ok; ++kb, ++kg) {
+          const int s = (int)(kg % stages);
+          if (kg >= stages)
+            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / stages) - 1) & 1), flag, 11);
           if (!ok) break;
           const uint32_t a = sbase + s * stage_bytes;  // [Ah][Al][Ch][Cl]
           const uint32_t bar = full0 + 8 * s;
-          mbar_arrive_expect_tx(bar, stage_bytes);
-          tma_load_2d(a, &mapAh, bar, kb * KE, (int)m0);
-          if (SPLIT == 3) tma_load_2d(a + a_bytes, &mapAl, bar, kb * KE, (int)m0);
-          tma_load_2d(a + NS * a_bytes, &mapCh, bar, kb * KE, c0);
-          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, &mapCl, bar, kb * KE, c0);
+          mbar_arrive_expect_tx(bar, tx);
+          tma_load_2d(a, T.Ah, bar, kb * KE, (int)T.m0);
+          if (SPLIT == 3) tma_load_2d(a + a_bytes, T.Al, bar, kb * KE, (int)T.m0);
+          tma_load_2d(a + NS * a_bytes, T.Ch, bar, kb * KE, c0);
+          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, T.Cl, bar, kb * KE, c0);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = KD::idesc(kBM, XN);
       int64_t kg = 0, g = 0;
-      for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const XTile T = loc.at(t);
+        const int kblocks = T.p->kblocks;
+        const int ngroups = (kblocks + kGroupKb - 1) / kGroupKb;
+        const uint32_t idesc = KD::idesc(kBM, T.xn);
         for (int gr = 0; gr < ngroups && ok; ++gr, ++g) {
           const int b = (int)(g & 1);
-          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 14);
+          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), flag, 14);
           if (!ok) break;
           tc_fence_after();
           const uint32_t d = tbase + b * XN;
-          const int kb0 = gr * kGroupKb, kb1 = min(p.kblocks, kb0 + kGroupKb);
+          const int kb0 = gr * kGroupKb, kb1 = min(kblocks, kb0 + kGroupKb);
           for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
-            const int s = (int)(kg % p.stages);
-            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / p.stages) & 1), p.flag, 12);
+            const int s = (int)(kg % stages);
+            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / stages) & 1), flag, 12);
             if (!ok) break;
             tc_fence_after();
             const uint32_t ah = sbase + s * stage_bytes, al = ah + a_bytes;
@@ -288,91 +319,135 @@ __global__ void __launch_bounds__(kThreads, 1)
     // epilogue warps: quadrant q of TMEM lanes, column half h
     const int q = warp & 3, h = (warp - 2) >> 2;
     int64_t g = 0;
-    for (int64_t t = blockIdx.x; t < p.tiles; t += gridDim.x) {
-      const int64_t m0 = p.row0 + (t / p.ncg) * kBM;
-      const int cg = (int)(t % p.ncg);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const XTile T = loc.at(t);
+      const XpassParams &p = *T.p;
+      const int half = T.xn / 2;  // a multiple of 16
+      const int ngroups = (p.kblocks + kGroupKb - 1) / kGroupKb;
+      const int64_t m0 = T.m0;
+      const int cg = T.cg;
       const int64_t row_end = p.row0 + p.rows;
-      float acc[HALF];
+      const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + 2 * XN + h * half;
+      float acc[AREG];
 #pragma unroll
-      for (int c = 0; c < HALF; ++c) acc[c] = 0.0f;
+      for (int c = 0; c < AREG; ++c) acc[c] = 0.0f;
       for (int gr = 0; gr < ngroups; ++gr, ++g) {
         const int b = (int)(g & 1);
-        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 13);
+        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), flag, 13);
         __syncwarp();
         tc_fence_after();
-        const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * XN + h * HALF;
-#pragma unroll
+        const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * XN + h * half;
+#pragma unroll (ACC_T ? 1 : HALF / 16)
         for (int c = 0; c < HALF; c += 16) {
-          float v[16];
-          tmem_ld16(ta + c, v);
+          if (c < half) {
+            float v[16];
+            tmem_ld16(ta + c, v);
+            if (ACC_T) {
+              if (gr > 0) {
+                float a[16];
+                tmem_ld16(tacc + c, a);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
+                for (int i = 0; i < 16; ++i) v[i] = a[i] + v[i];
+              }
+              tmem_st16(tacc + c, v);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) acc[(c + i) % AREG] += v[i];
+            }
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
+      // the 16 accumulated columns c .. c + 15 of this thread's half
+      auto acc16 = [&](int c, float *a) {
+        if (ACC_T) {
+          tmem_ld16(tacc + c, a);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) a[i] = acc[(c + i) % AREG];
+        }
+      };
       const int64_t row = m0 + q * 32 + lane;
       if (KIND == kKindF16 && ok && row < row_end) {
         // scaled X split into FP16 hi + lo (each rounded to nearest), and the
         // fused w partial sum_i X[row][i] C[mu][i] of the unscaled X
         const float xo = p.scale->x_out, xu = p.scale->x_unscale;
         const int mu = (int)(row % p.n);
-        const int col = cg * XN + h * HALF;
+        const int col = cg * T.xn + h * half;
         __half *xh = p.Xh16 + row * p.ldx + col;
         __half *xl = p.Xl16 + row * p.ldx + col;
         const float *cr = p.Cf + (int64_t)mu * p.ldx + col;
         float wsum = 0.0f;
+#pragma unroll (ACC_T ? 1 : HALF / 16)
+        for (int c16 = 0; c16 < HALF; c16 += 16) {
+          if (c16 < half) {
+            float a16[16];
+            acc16(c16, a16);
 #pragma unroll
-        for (int c = 0; c < HALF; c += 8) {
-          const float4 ca = *reinterpret_cast<const float4 *>(cr + c);
-          const float4 cb = *reinterpret_cast<const float4 *>(cr + c + 4);
-          wsum = fmaf(acc[c], ca.x, wsum);
-          wsum = fmaf(acc[c + 1], ca.y, wsum);
-          wsum = fmaf(acc[c + 2], ca.z, wsum);
-          wsum = fmaf(acc[c + 3], ca.w, wsum);
-          wsum = fmaf(acc[c + 4], cb.x, wsum);
-          wsum = fmaf(acc[c + 5], cb.y, wsum);
-          wsum = fmaf(acc[c + 6], cb.z, wsum);
-          wsum = fmaf(acc[c + 7], cb.w, wsum);
-          __align__(16) __half hv[8], lv[8];
+            for (int e = 0; e < 16; e += 8) {
+              const int c = c16 + e;
+              const float *av = a16 + e;
+              const float4 ca = *reinterpret_cast<const float4 *>(cr + c);
+              const float4 cb = *reinterpret_cast<const float4 *>(cr + c + 4);
+              wsum = fmaf(av[0], ca.x, wsum);
+              wsum = fmaf(av[1], ca.y, wsum);
+              wsum = fmaf(av[2], ca.z, wsum);
+              wsum = fmaf(av[3], ca.w, wsum);
+              wsum = fmaf(av[4], cb.x, wsum);
+              wsum = fmaf(av[5], cb.y, wsum);
+              wsum = fmaf(av[6], cb.z, wsum);
+              wsum = fmaf(av[7], cb.w, wsum);
+              __align__(16) __half hv[8], lv[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float v = acc[c + k] * xo;
-            hv[k] = __float2half_rn(v);
-            lv[k] = __float2half_rn(v - __half2float(hv[k]));
+              for (int k = 0; k < 8; ++k) {
+                const float v = av[k] * xo;
+                hv[k] = __float2half_rn(v);
+                lv[k] = __float2half_rn(v - __half2float(hv[k]));
+              }
+              *reinterpret_cast<uint4 *>(xh + c) = *reinterpret_cast<const uint4 *>(hv);
+              *reinterpret_cast<uint4 *>(xl + c) = *reinterpret_cast<const uint4 *>(lv);
+            }
           }
-          *reinterpret_cast<uint4 *>(xh + c) = *reinterpret_cast<const uint4 *>(hv);
-          *reinterpret_cast<uint4 *>(xl + c) = *reinterpret_cast<const uint4 *>(lv);
         }
         p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum * xu;
       }
       if (KIND == kKindTF32 && EPI == 0 && ok && row < row_end) {
         const int mu = (int)(row % p.n);
-        const int col = cg * XN + h * HALF;
+        const int col = cg * T.xn + h * half;
         float *xh = p.Xh + row * p.ldx + col;
         float *xl = p.Xl + row * p.ldx + col;
         const float *cr = p.Cf + (int64_t)mu * p.ldx + col;
         float wsum = 0.0f;
+#pragma unroll (ACC_T ? 1 : HALF / 16)
+        for (int c16 = 0; c16 < HALF; c16 += 16) {
+          if (c16 < half) {
+            float a16[16];
+            acc16(c16, a16);
 #pragma unroll
-        for (int c = 0; c < HALF; c += 4) {
-          const float4 cc = *reinterpret_cast<const float4 *>(cr + c);
-          wsum = fmaf(acc[c], cc.x, wsum);
-          wsum = fmaf(acc[c + 1], cc.y, wsum);
-          wsum = fmaf(acc[c + 2], cc.z, wsum);
-          wsum = fmaf(acc[c + 3], cc.w, wsum);
-          float4 hv, lv;
-          hv.x = tf32r(acc[c]);
-          hv.y = tf32r(acc[c + 1]);
-          hv.z = tf32r(acc[c + 2]);
-          hv.w = tf32r(acc[c + 3]);
-          *reinterpret_cast<float4 *>(xh + c) = hv;
-          if (SPLIT == 3) {
-            lv.x = tf32r(acc[c] - hv.x);
-            lv.y = tf32r(acc[c + 1] - hv.y);
-            lv.z = tf32r(acc[c + 2] - hv.z);
-            lv.w = tf32r(acc[c + 3] - hv.w);
-            *reinterpret_cast<float4 *>(xl + c) = lv;
+            for (int e = 0; e < 16; e += 4) {
+              const int c = c16 + e;
+              const float *av = a16 + e;
+              const float4 cc = *reinterpret_cast<const float4 *>(cr + c);
+              wsum = fmaf(av[0], cc.x, wsum);
+              wsum = fmaf(av[1], cc.y, wsum);
+              wsum = fmaf(av[2], cc.z, wsum);
+              wsum = fmaf(av[3], cc.w, wsum);
+              float4 hv, lv;
+              hv.x = tf32r(av[0]);
+              hv.y = tf32r(av[1]);
+              hv.z = tf32r(av[2]);
+              hv.w = tf32r(av[3]);
+              *reinterpret_cast<float4 *>(xh + c) = hv;
+              if (SPLIT == 3) {
+                lv.x = tf32r(av[0] - hv.x);
+                lv.y = tf32r(av[1] - hv.y);
+                lv.z = tf32r(av[2] - hv.z);
+                lv.w = tf32r(av[3] - hv.w);
+                *reinterpret_cast<float4 *>(xl + c) = lv;
+              }
+            }
           }
         }
         p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum;
@@ -380,14 +455,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (KIND == kKindTF32 && EPI == 1 && ok && row < row_end && (int)(row % p.bk) < p.bkv) {
         // consecutive lanes hold consecutive q of one mu: coalesced per column
         const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
-        const int col = cg * XN + h * HALF;
+        const int col = cg * T.xn + h * half;
         const int64_t base = ((qq >> 5) * p.xrows + (int64_t)col * p.n + mu) * 32 + (qq & 31);
         const int64_t step = (int64_t)p.n * 32;
+#pragma unroll (ACC_T ? 1 : HALF / 16)
+        for (int c16 = 0; c16 < HALF; c16 += 16) {
+          if (c16 < half) {
+            float a16[16];
+            acc16(c16, a16);
 #pragma unroll
-        for (int c = 0; c < HALF; ++c) {
-          const float hv = tf32r(acc[c]);
-          p.Xh[base + (int64_t)c * step] = hv;
-          if (SPLIT == 3) p.Xl[base + (int64_t)c * step] = tf32r(acc[c] - hv);
+            for (int e = 0; e < 16; ++e) {
+              const int c = c16 + e;
+              const float hv = tf32r(a16[e]);
+              p.Xh[base + (int64_t)c * step] = hv;
+              if (SPLIT == 3) p.Xl[base + (int64_t)c * step] = tf32r(a16[e] - hv);
+            }
+          }
         }
       }
     }
@@ -397,10 +480,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
 
+template <int KIND, int XN, int SPLIT, int EPI>
+__global__ void __launch_bounds__(kThreads, xpass_min_blocks(XN))
+    k_xpass(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+            const __grid_constant__ CUtensorMap mapCh, const __grid_constant__ CUtensorMap mapCl,
+            const __grid_constant__ XpassParams p) {
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapAh);
+    prefetch_tmap(&mapCh);
+    if (SPLIT == 3) {
+      prefetch_tmap(&mapAl);
+      prefetch_tmap(&mapCl);
+    }
+  }
+  const XLocOne<XN> loc{&mapAh, &mapAl, &mapCh, &mapCl, &p};
+  xpass_body<KIND, XN, SPLIT, EPI>(loc, p.tiles, p.stages, p.flag);
+}
+
 // w[P] = sum over partials and mu of wpart[k][P*N + mu] (FP64); also fp32 w.
-__global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t rows, int nparts,
-                                                 int n, double *w, float *w32, int P0) {
-  const int P = P0 + blockIdx.x;
+// One 256-thread block per P.
+__device__ __forceinline__ void wreduce_one(const float *wpart, int64_t rows, int nparts, int n,
+                                            double *w, float *w32, int P) {
   double s = 0.0;
   for (int g = 0; g < nparts; ++g)
     for (int m = threadIdx.x; m < n; m += blockDim.x) s += wpart[g * rows + (int64_t)P * n + m];
@@ -415,6 +515,11 @@ __global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t row
     w[P] = red[0];
     w32[P] = (float)red[0];
   }
+}
+
+__global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t rows, int nparts,
+                                                 int n, double *w, float *w32, int P0) {
+  wreduce_one(wpart, rows, nparts, n, w, w32, P0 + blockIdx.x);
 }
 
 // ---------------------------------------------------------------- SYRK ---
@@ -450,35 +555,43 @@ __device__ __forceinline__ void tile_of(int t, int &tm, int &tn) {
 
 constexpr int kSyCols = kBM / (kEpiWarps / 4);  // columns per epilogue thread
 constexpr uint32_t kLoCol = 2 * kBM;             // TMEM columns of the compensation term
+constexpr uint32_t kHiCol = 3 * kBM;             // TMEM columns of the running sum
 
-// Persistent SYRK over work items (lower tile, aux chunk); item i -> tile
-// i % ntri, chunk i / ntri.  Partial tiles are written in FP64.  KIND: TF32
+// One SYRK work item: operand maps, problem parameters, lower tile and aux
+// chunk.
+struct SyItem {
+  const CUtensorMap *Xh, *Xl, *Yh, *Yl;
+  const SyrkParams *p;
+  int tile, chunk;
+};
+
+// Work-item locator of a single-problem launch: item i -> tile i % ntri,
+// chunk i / ntri.
+struct SyLocOne {
+  const CUtensorMap *Xh, *Xl, *Yh, *Yl;
+  const SyrkParams *p;
+  __device__ __forceinline__ SyItem at(int it) const {
+    return SyItem{Xh, Xl, Yh, Yl, p, it % p->ntri, it / p->ntri};
+  }
+};
+
+// Persistent SYRK over work items (lower tile, aux chunk).  Partial tiles are written in FP64.  KIND: TF32
 // or FP16 operands (the blocked operand mode of direct mode is TF32 only).
-template <int KIND, int SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_syrk(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
-           const __grid_constant__ CUtensorMap mapYh, const __grid_constant__ CUtensorMap mapYl,
-           const SyrkParams p) {
+template <int KIND, int SPLIT, class LOC>
+__device__ __forceinline__ void syrk_body(const LOC &loc, int items, int stages, int *flag) {
   using KD = Kind<KIND>;
   constexpr int KE = KD::kElems;
   constexpr int NS = SPLIT == 3 ? 2 : 1;
   constexpr uint32_t stage_bytes = NS * 2 * kAStage;  // [Xh(tm)][Xh(tn)][Xl(tm)][Xl(tn)]
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * stage_bytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 4);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * p.stages;
-  const uint32_t tfull0 = full0 + 16 * p.stages, tempty0 = tfull0 + 16;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * stages;
+  const uint32_t tfull0 = full0 + 16 * stages, tempty0 = tfull0 + 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = p.ntri * p.nchunk;
   if (threadIdx.x == 0) {
-    prefetch_tmap(&mapXh);
-    if (SPLIT == 3) prefetch_tmap(&mapXl);
-    if (p.two) {
-      prefetch_tmap(&mapYh);
-      prefetch_tmap(&mapYl);
-    }
-    for (int s = 0; s < p.stages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -495,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t sbase = smem_u32(smem);
   bool ok = true;
   // chunk ch -> first aux function P0 (3-D mode) or first k-block (2-D mode), k-block count
-  auto chunk_kb = [&](int ch, int64_t &P0, int &nkb) {
+  auto chunk_kb = [&](const SyrkParams &p, int ch, int64_t &P0, int &nkb) {
     if (p.mode2d) {
       P0 = (int64_t)ch * p.kb_per_chunk;
       nkb = (int)max((int64_t)0, min(p.kb_total, P0 + p.kb_per_chunk) - P0);
@@ -509,14 +622,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int64_t kg = 0;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const SyItem I = loc.at(it);
+        const SyrkParams &p = *I.p;
         int tm, tn, nkb;
         int64_t P0;
-        tile_of(it % p.ntri, tm, tn);
-        chunk_kb(it / p.ntri, P0, nkb);
+        tile_of(I.tile, tm, tn);
+        chunk_kb(p, I.chunk, P0, nkb);
         for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
-          const int s = (int)(kg % p.stages);
-          if (kg >= p.stages)
-            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / p.stages) - 1) & 1), p.flag, 21);
+          const int s = (int)(kg % stages);
+          if (kg >= stages)
+            ok = mbar_wait(empty0 + 8 * s, (uint32_t)(((kg / stages) - 1) & 1), flag, 21);
           if (!ok) break;
           const uint32_t a = sbase + s * stage_bytes, bar = full0 + 8 * s;
           mbar_arrive_expect_tx(bar, stage_bytes);
@@ -524,11 +639,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             // one box = 128 consecutive mu of one (i, P block): 16 KB contiguous
             const int64_t kk = P0 + kb;
             const int pb = (int)(kk % p.npb), ii = (int)(kk / p.npb);
-            tma_load_4d(a, &mapXh, bar, 0, tm * kBM, ii, pb);
-            tma_load_4d(a + kAStage, &mapXh, bar, 0, tn * kBM, ii, pb);
+            tma_load_4d(a, I.Xh, bar, 0, tm * kBM, ii, pb);
+            tma_load_4d(a + kAStage, I.Xh, bar, 0, tn * kBM, ii, pb);
             if (SPLIT == 3) {
-              tma_load_4d(a + 2 * kAStage, &mapXl, bar, 0, tm * kBM, ii, pb);
-              tma_load_4d(a + 3 * kAStage, &mapXl, bar, 0, tn * kBM, ii, pb);
+              tma_load_4d(a + 2 * kAStage, I.Xl, bar, 0, tm * kBM, ii, pb);
+              tma_load_4d(a + 3 * kAStage, I.Xl, bar, 0, tn * kBM, ii, pb);
             }
           } else {
             const int half = p.two ? nkb / 2 : nkb;
@@ -536,10 +651,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int kk = second ? kb - half : kb;
             const int P = (int)P0 + kk / p.nib, i0 = (kk % p.nib) * KE;
             // one-operand: X[tm], X[tn]; two-operand: X[tm], Y[tn] then Y[tm], X[tn]
-            const CUtensorMap *mh = (p.two && second) ? &mapYh : &mapXh;
-            const CUtensorMap *ml = (p.two && second) ? &mapYl : &mapXl;
-            const CUtensorMap *nh = (p.two && !second) ? &mapYh : &mapXh;
-            const CUtensorMap *nl = (p.two && !second) ? &mapYl : &mapXl;
+            const CUtensorMap *mh = (p.two && second) ? I.Yh : I.Xh;
+            const CUtensorMap *ml = (p.two && second) ? I.Yl : I.Xl;
+            const CUtensorMap *nh = (p.two && !second) ? I.Yh : I.Xh;
+            const CUtensorMap *nl = (p.two && !second) ? I.Yl : I.Xl;
             tma_load_3d(a, mh, bar, i0, tm * kBM, P);
             tma_load_3d(a + kAStage, nh, bar, i0, tn * kBM, P);
             if (SPLIT == 3) {
@@ -555,19 +670,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = KD::idesc(kBM, kBM);
       int64_t kg = 0, g = 0;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const SyItem I = loc.at(it);
         int nkb;
         int64_t P0;
-        chunk_kb(it / p.ntri, P0, nkb);
+        chunk_kb(*I.p, I.chunk, P0, nkb);
         for (int kb0 = 0; kb0 < nkb && ok; kb0 += kGroupKbS, ++g) {
           const int b = (int)(g & 1);
-          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), p.flag, 24);
+          if (g >= 2) ok = mbar_wait(tempty0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), flag, 24);
           if (!ok) break;
           tc_fence_after();
           const uint32_t d = tbase + b * kBM;
           const int kb1 = min(nkb, kb0 + kGroupKbS);
           for (int kb = kb0; kb < kb1 && ok; ++kb, ++kg) {
-            const int s = (int)(kg % p.stages);
-            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / p.stages) & 1), p.flag, 22);
+            const int s = (int)(kg % stages);
+            ok = mbar_wait(full0 + 8 * s, (uint32_t)((kg / stages) & 1), flag, 22);
             if (!ok) break;
             tc_fence_after();
             const uint32_t hm = sbase + s * stage_bytes, hn = hm + kAStage;
@@ -600,39 +716,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     int64_t g = 0;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      const SyItem I = loc.at(it);
+      const SyrkParams &p = *I.p;
       int nkb;
       int64_t P0;
-      chunk_kb(it / p.ntri, P0, nkb);
-      float hi[kSyCols];
-#pragma unroll
-      for (int c = 0; c < kSyCols; ++c) hi[c] = 0.0f;
-      {  // zero the compensation columns
+      chunk_kb(p, I.chunk, P0, nkb);
+      // float-float running sum (hi, lo) of the chains, both halves in TMEM
+      const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+      const uint32_t th = tbase + lane_base + kHiCol + h * kSyCols;
+      {
         float z[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) z[i] = 0.0f;
 #pragma unroll
-        for (int c = 0; c < kSyCols; c += 16) tmem_st16(tbase + lane_base + kLoCol + h * kSyCols + c, z);
+        for (int c = 0; c < kSyCols; c += 16) {
+          tmem_st16(tl + c, z);
+          tmem_st16(th + c, z);
+        }
       }
       for (int kb0 = 0; kb0 < nkb; kb0 += kGroupKbS, ++g) {
         const int b = (int)(g & 1);
-        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), p.flag, 23);
+        if (ok) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)((g >> 1) & 1), flag, 23);
         __syncwarp();
         tc_fence_after();
         const uint32_t ta = tbase + lane_base + b * kBM + h * kSyCols;
-        const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < kSyCols; c += 16) {
-          float v[16], lo[16];
+          float v[16], lo[16], hi[16];
           tmem_ld16(ta + c, v);
           tmem_ld16(tl + c, lo);
+          tmem_ld16(th + c, hi);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {  // two-sum: (hi, lo) += v
-            const float s = hi[c + i] + v[i];
-            const float bp = s - hi[c + i];
-            lo[i] += (hi[c + i] - (s - bp)) + (v[i] - bp);
-            hi[c + i] = s;
+            const float s = hi[i] + v[i];
+            const float bp = s - hi[i];
+            lo[i] += (hi[i] - (s - bp)) + (v[i] - bp);
+            hi[i] = s;
           }
           tmem_st16(tl + c, lo);
+          tmem_st16(th + c, hi);
         }
         tc_fence_before();
         __syncwarp();
@@ -640,18 +762,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int r = q * 32 + lane;
       double *dst =
-          p.part + (((int64_t)(it / p.ntri) * p.ntri + it % p.ntri) * kBM + r) * kBM + h * kSyCols;
-      const uint32_t tl = tbase + lane_base + kLoCol + h * kSyCols;
+          p.part + (((int64_t)I.chunk * p.ntri + I.tile) * kBM + r) * kBM + h * kSyCols;
       const double ku = (KIND == kKindF16) ? p.scale->k_unscale : 1.0;
-#pragma unroll
+#pragma unroll 1
       for (int c = 0; c < kSyCols; c += 16) {
-        float lo[16];
+        float lo[16], hi[16];
         tmem_ld16(tl + c, lo);
+        tmem_ld16(th + c, hi);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
           const double2 v =
-              make_double2(ok ? ((double)hi[c + i] + (double)lo[i]) * ku : 0.0,
-                           ok ? ((double)hi[c + i + 1] + (double)lo[i + 1]) * ku : 0.0);
+              make_double2(ok ? ((double)hi[i] + (double)lo[i]) * ku : 0.0,
+                           ok ? ((double)hi[i + 1] + (double)lo[i + 1]) * ku : 0.0);
           *reinterpret_cast<double2 *>(dst + c + i) = v;
         }
       }
@@ -660,6 +782,102 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
+template <int KIND, int SPLIT>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_syrk(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
+           const __grid_constant__ CUtensorMap mapYh, const __grid_constant__ CUtensorMap mapYl,
+           const __grid_constant__ SyrkParams p) {
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapXh);
+    if (SPLIT == 3) prefetch_tmap(&mapXl);
+    if (p.two) {
+      prefetch_tmap(&mapYh);
+      prefetch_tmap(&mapYl);
+    }
+  }
+  const SyLocOne loc{&mapXh, &mapXl, &mapYh, &mapYl, &p};
+  syrk_body<KIND, SPLIT>(loc, p.ntri * p.nchunk, p.stages, p.flag);
+}
+
+// ------------------------------------------------- grouped (serving) ---
+//
+// Several independent molecules' X passes (or SYRKs) in one persistent
+// launch: the problem table travels as one kernel parameter (tensor maps
+// included, so the TMA reads them from parameter space and nothing is
+// uploaded), and the locator maps a global tile index to its problem by the
+// table's prefix of tile counts.  Each problem keeps its own plan (column
+// groups, tile width, k-blocks, aux chunks), so every tile computes exactly
+// what the single-problem launch computes for it.
+
+struct XGroupProb {  // tensor maps first (128-byte aligned)
+  CUtensorMap Ah, Al, Ch, Cl;
+  XpassParams p;
+  int xn;
+};
+
+struct XGroupTab {
+  XGroupProb prob[kMaxGroup];
+  int64_t tile0[kMaxGroup + 1];  // prefix of the problems' tile counts
+  int nprob, stages;
+  int *flag;
+};
+
+template <int XN> struct XLocGroup {
+  const XGroupTab *g;
+  __device__ __forceinline__ XTile at(int64_t t) const {
+    int k = 0;
+    while (k + 1 < g->nprob && t >= g->tile0[k + 1]) ++k;
+    const XGroupProb &q = g->prob[k];
+    const int64_t lt = t - g->tile0[k];
+    return XTile{&q.Ah, &q.Al, &q.Ch, &q.Cl, &q.p, q.p.row0 + (lt / q.p.ncg) * kBM,
+                 (int)(lt % q.p.ncg), q.xn};
+  }
+};
+
+template <int XN>
+__global__ void __launch_bounds__(kThreads, xpass_min_blocks(XN))
+    k_xpass_grp(const __grid_constant__ XGroupTab g) {
+  if (threadIdx.x < 4 * g.nprob) {
+    const XGroupProb &q = g.prob[threadIdx.x >> 2];
+    const int m = threadIdx.x & 3;
+    prefetch_tmap(m == 0 ? &q.Ah : m == 1 ? &q.Al : m == 2 ? &q.Ch : &q.Cl);
+  }
+  const XLocGroup<XN> loc{&g};
+  xpass_body<kKindF16, XN, 3, 0>(loc, g.tile0[g.nprob], g.stages, g.flag);
+}
+
+struct SyGroupProb {
+  CUtensorMap Xh, Xl;
+  SyrkParams p;
+};
+
+struct SyGroupTab {
+  SyGroupProb prob[kMaxGroup];
+  int item0[kMaxGroup + 1];  // prefix of the problems' work items
+  int nprob, stages;
+  int *flag;
+};
+
+struct SyLocGroup {
+  const SyGroupTab *g;
+  __device__ __forceinline__ SyItem at(int it) const {
+    int k = 0;
+    while (k + 1 < g->nprob && it >= g->item0[k + 1]) ++k;
+    const SyGroupProb &q = g->prob[k];
+    const int lt = it - g->item0[k];
+    return SyItem{&q.Xh, &q.Xl, &q.Xh, &q.Xl, &q.p, lt % q.p.ntri, lt / q.p.ntri};
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 2) k_syrk_grp(const __grid_constant__ SyGroupTab g) {
+  if (threadIdx.x < 2 * g.nprob) {
+    const SyGroupProb &q = g.prob[threadIdx.x >> 1];
+    prefetch_tmap((threadIdx.x & 1) ? &q.Xl : &q.Xh);
+  }
+  const SyLocGroup loc{&g};
+  syrk_body<kKindF16, 3>(loc, g.item0[g.nprob], g.stages, g.flag);
 }
 
 // C = scale * A B^T for row ranges of two K-major split-FP16 operands (the
@@ -837,10 +1055,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // K = sum over chunks of the FP64 partial tiles, symmetric.  One block per
 // (lower tile, 32-row strip): sums into shared memory, writes the strip and
 // its mirror image coalesced.
-__global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nchunk, int ntri,
-                                                     int n, double *K) {
+__device__ __forceinline__ void syrk_reduce_strip(const double *part, int nchunk, int ntri, int n,
+                                                  double *K, int t, int sr) {
   __shared__ double strip[32][kBM + 1];
-  const int t = blockIdx.x, sr = blockIdx.y;
   int tm = 0;
   while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
   const int tn = t - tm * (tm + 1) / 2;
@@ -862,6 +1079,11 @@ __global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nch
     const int mu = tm * kBM + sr * 32 + rr, nu = tn * kBM + c;
     if (mu < n && nu < n && (tm != tn || nu < mu)) K[(int64_t)nu * n + mu] = strip[rr][c];
   }
+}
+
+__global__ void __launch_bounds__(256) k_syrk_reduce(const double *part, int nchunk, int ntri,
+                                                     int n, double *K) {
+  syrk_reduce_strip(part, nchunk, ntri, n, K, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- TRMM ---
@@ -1769,6 +1991,193 @@ int jk_k_rank2(Df *df, const double *Cw, const double *Cd, double *K, cudaStream
                     ms->scaleK.as<MixScale>());
 }
 
+// ------------------------------------------- grouped passes (serving) ---
+
+// Small reductions of a group: one launch, blockIdx.y (w) or blockIdx.z (K)
+// selects the problem; blocks past a problem's own extent return at once.
+struct WredGroup {
+  const float *wpart[kMaxGroup];
+  double *w[kMaxGroup];
+  float *w32[kMaxGroup];
+  int64_t rows[kMaxGroup];
+  int nparts[kMaxGroup], n[kMaxGroup], naux[kMaxGroup];
+};
+
+__global__ void __launch_bounds__(256) k_wreduce_grp(const __grid_constant__ WredGroup g) {
+  const int k = blockIdx.y;
+  if ((int)blockIdx.x >= g.naux[k]) return;
+  wreduce_one(g.wpart[k], g.rows[k], g.nparts[k], g.n[k], g.w[k], g.w32[k], blockIdx.x);
+}
+
+struct SyRedGroup {
+  const double *part[kMaxGroup];
+  double *K[kMaxGroup];
+  int nchunk[kMaxGroup], ntri[kMaxGroup], n[kMaxGroup];
+};
+
+__global__ void __launch_bounds__(256) k_syrk_reduce_grp(const __grid_constant__ SyRedGroup g) {
+  const int k = blockIdx.z;
+  if ((int)blockIdx.x >= g.ntri[k]) return;
+  syrk_reduce_strip(g.part[k], g.nchunk[k], g.ntri[k], g.n[k], g.K[k], blockIdx.x, blockIdx.y);
+}
+
+static bool groupable(const Df *df) {
+  const MixedState *ms = df->mixed.get();
+  return df->mode == BQC_DF_STORED && ms && ms->shadow == BQC_SHADOW_F16 && !df->is_shard() &&
+         df->B64.p;
+}
+
+int group_prep(Df *df, const double *C, cudaStream_t s) {
+  if (!groupable(df)) {
+    set_error("grouped builds need a stored, unsharded handle with FP16 shadows", __FILE__,
+              __LINE__);
+    return BQC_E_UNSUPPORTED;
+  }
+  MixedState *ms = df->mixed.get();
+  const int64_t rows = (int64_t)df->naux_loc * df->basis->nbf;
+  return mixed_xpass(df, C, kKindF16, 3, s, &ms->mapAh, &ms->mapAl, rows, nullptr, nullptr,
+                     nullptr, 0, 0, true);
+}
+
+template <int XN>
+static int xpass_grp_launch(const XGroupTab &tab, size_t smem, int grid, cudaStream_t s) {
+  BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_grp<XN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  k_xpass_grp<XN><<<grid, kThreads, smem, s>>>(tab);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+// X pass and w of n problems (their C split by group_prep) in one launch
+// each: X into each handle's FP16 X split, w into df->w.
+int group_xpass(Df *const *dfs, int n, cudaStream_t s) {
+  if (n <= 0 || n > kMaxGroup) return BQC_E_INVALID;
+  int xnmax = 0, naux_max = 0;
+  for (int k = 0; k < n; ++k) {
+    if (!groupable(dfs[k])) return BQC_E_UNSUPPORTED;
+    xnmax = std::max(xnmax, dfs[k]->mixed->plan.xn);
+    naux_max = std::max(naux_max, dfs[k]->naux_loc);
+  }
+  const int XN = xnmax <= 64 ? 64 : xnmax <= 128 ? 128 : 256;
+  auto tab = std::make_unique<XGroupTab>();
+  std::memset(tab.get(), 0, sizeof(XGroupTab));
+  auto wr = std::make_unique<WredGroup>();
+  std::memset(wr.get(), 0, sizeof(WredGroup));
+  int64_t t0 = 0;
+  for (int k = 0; k < n; ++k) {
+    Df *df = dfs[k];
+    MixedState *ms = df->mixed.get();
+    const MixedPlan &m = ms->plan;
+    const int nb = df->basis->nbf, naux = df->naux_loc;
+    XGroupProb &q = tab->prob[k];
+    q.Ah = ms->mapAh;
+    q.Al = ms->mapAl;
+    q.Ch = ms->mapCh;
+    q.Cl = ms->mapCl;
+    q.xn = m.xn;
+    XpassParams &p = q.p;
+    p.row0 = 0;
+    p.rows = (int64_t)naux * nb;
+    p.wstride = p.rows;
+    p.n = nb;
+    p.ldx = m.ldx;
+    p.ncg = m.ncg;
+    p.kblocks = (m.ld16 + 63) / 64;
+    p.stages = 0;  // the group's
+    p.tiles = (p.rows + kBM - 1) / kBM * m.ncg;
+    p.Xh16 = ms->Xh16.as<__half>();
+    p.Xl16 = ms->Xl16.as<__half>();
+    p.scale = ms->scale.as<MixScale>();
+    p.Cf = ms->Cf.as<float>();
+    p.wpart = ms->wpart.as<float>();
+    p.flag = df->ctx->flag;
+    tab->tile0[k] = t0;
+    t0 += p.tiles;
+    wr->wpart[k] = ms->wpart.as<float>();
+    wr->w[k] = df->w.as<double>();
+    wr->w32[k] = ms->w32.as<float>();
+    wr->rows[k] = p.rows;
+    wr->nparts[k] = 2 * m.ncg;
+    wr->n[k] = nb;
+    wr->naux[k] = naux;
+  }
+  tab->tile0[n] = t0;
+  tab->nprob = n;
+  tab->flag = dfs[0]->ctx->flag;
+  const size_t stage = 2 * ((size_t)kAStage + (size_t)XN * 128);
+  tab->stages = (int)std::min<size_t>(8, (232448 - 1024 - 256) / stage);
+  const size_t smem = tab->stages * stage + 1024 + 256;
+  const int grid = (int)std::min<int64_t>(sm_count(), t0);
+  if (grid > 0) {
+    if (XN == 64) BQC_TRY(xpass_grp_launch<64>(*tab, smem, grid, s));
+    else if (XN == 128) BQC_TRY(xpass_grp_launch<128>(*tab, smem, grid, s));
+    else BQC_TRY(xpass_grp_launch<256>(*tab, smem, grid, s));
+  }
+  k_wreduce_grp<<<dim3((unsigned)naux_max, (unsigned)n), 256, 0, s>>>(*wr);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+// K of n problems from their X split (group_xpass) in one SYRK launch and
+// one reduction launch.
+int group_syrk(Df *const *dfs, double *const *K, int n, cudaStream_t s) {
+  if (n <= 0 || n > kMaxGroup) return BQC_E_INVALID;
+  auto tab = std::make_unique<SyGroupTab>();
+  std::memset(tab.get(), 0, sizeof(SyGroupTab));
+  auto red = std::make_unique<SyRedGroup>();
+  std::memset(red.get(), 0, sizeof(SyRedGroup));
+  int items = 0, ntri_max = 0;
+  for (int k = 0; k < n; ++k) {
+    Df *df = dfs[k];
+    if (!groupable(df)) return BQC_E_UNSUPPORTED;
+    MixedState *ms = df->mixed.get();
+    const MixedPlan &m = ms->plan;
+    SyGroupProb &g = tab->prob[k];
+    g.Xh = ms->mapXh;
+    g.Xl = ms->mapXl;
+    SyrkParams &q = g.p;
+    q.n = df->basis->nbf;
+    q.ldx = m.ldx;
+    q.naux = df->naux_loc;
+    q.ntri = m.ntri;
+    q.p_per_chunk = m.ppc;
+    q.nchunk = (q.naux + m.ppc - 1) / m.ppc;
+    q.nib = (m.ldx + 63) / 64;
+    q.stages = 0;  // the group's
+    q.part = df->Kpart.as<double>();
+    q.flag = df->ctx->flag;
+    q.scale = ms->scale.as<MixScale>();
+    q.two = 0;
+    q.mode2d = 0;
+    q.npb = 0;
+    q.kb_total = 0;
+    q.kb_per_chunk = 0;
+    tab->item0[k] = items;
+    items += q.ntri * q.nchunk;
+    red->part[k] = q.part;
+    red->K[k] = K[k];
+    red->nchunk[k] = q.nchunk;
+    red->ntri[k] = q.ntri;
+    red->n[k] = q.n;
+    ntri_max = std::max(ntri_max, q.ntri);
+  }
+  tab->item0[n] = items;
+  tab->nprob = n;
+  tab->flag = dfs[0]->ctx->flag;
+  const MixedPlan &m0 = dfs[0]->mixed->plan;  // the SYRK stage size is the same for every plan
+  tab->stages = m0.sy_stages[1];
+  const int grid = std::min(sm_count(), items);
+  if (grid > 0) {
+    BQC_CUDA_TRY(cudaFuncSetAttribute(k_syrk_grp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)m0.sy_smem[1]));
+    k_syrk_grp<<<grid, kThreads, m0.sy_smem[1], s>>>(*tab);
+    BQC_LAUNCH_CHECK();
+  }
+  k_syrk_reduce_grp<<<dim3((unsigned)ntri_max, kBM / 32, (unsigned)n), 256, 0, s>>>(*red);
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
 // w comes fused from the X pass in every mixed precision (FP32 row partials
 // of X C, summed in FP64).  The J pass then runs on the side stream beside
 // the tensor-core passes: the three-product builds read the packed FP64 B
@@ -1791,6 +2200,7 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     return BQC_E_INVALID;
   }
   const int split = prec == BQC_PREC_MIXED_TF32 ? 1 : 3;
+  if (kind == kKindF16 && df->group) return jk_grouped(df, C, J, K, s);
   const MixedPlan &m = ms->plan;
   const Basis *b = df->basis;
   const int n = b->nbf, naux = df->naux_loc;
@@ -2099,7 +2509,7 @@ int direct_mixed_prep_c(Df *df, const double *C, int split, cudaStream_t s) {
 int direct_mixed_block(Df *df, const double *raw, int q0, int nq, int split, cudaStream_t s) {
   DirectMixed *dm = df->dmixed.get();
   const MixedPlan &m = dm->plan;
-  const int n = df->basis->nbf, naux = df->basis->naux;
+  const int n = df->basis->nbf;
   const int k = split == 3 ? 1 : 0;
   for (int qs = 0; qs < nq; qs += dm->bs) {
     const int nv = std::min(dm->bs, nq - qs);
