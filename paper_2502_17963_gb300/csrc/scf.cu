@@ -97,6 +97,17 @@ __global__ void k_procrustes_pair(int n, int no, const double *Ca, const double 
   Cd[i] = t - a;
 }
 
+// W[:, j] = V[:, j] / sqrt(lam[j]) (column-major no x no)
+__global__ void k_scale_cols_rsqrt(int no, const double *V, const double *lam, double *W) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)no * no) return;
+  W[i] = V[i] / sqrt(lam[i / no]);
+}
+
+// incremental_build's answer when the increment cannot be formed: the
+// iteration is built in full instead
+constexpr int kIncFull = 1;
+
 // F = Fref + 2 (Jp - Jm) - (Kp - Km)
 __global__ void k_inc_fock(int64_t n, const double *Fref, const double *Jp, const double *Jm,
                            const double *Kp, const double *Km, double *F) {
@@ -285,8 +296,7 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   // orbitals, the Procrustes rotation and its work space
   const bool rank2 = inc_on && mixed_prec == BQC_PREC_MIXED_F16X3 &&
                      df->mode == BQC_DF_STORED && df->B64.p && df->mixed && !df->is_shard();
-  DBuf Ca, Sca, Mo, Uo, VTo, So, Ro, Ct, svdw, svdinfo;
-  int svd_lwork = 0;
+  DBuf Ca, Sca, Mo, Uo, VTo, So, Ro, Ct;
   if (inc_on) {
     for (DBuf *p : {&Facc, &Dref, &Dk, &J2, &K2, &Jx}) BQC_TRY(p->alloc(ctx, nn * 8));
     BQC_TRY(evd.alloc(ctx, (size_t)n * 8));
@@ -299,15 +309,12 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     for (DBuf *p : {&Ca, &Sca, &Ct}) BQC_TRY(p->alloc(ctx, on));
     for (DBuf *p : {&Mo, &Uo, &VTo, &Ro}) BQC_TRY(p->alloc(ctx, oo));
     BQC_TRY(So.alloc(ctx, (size_t)no * 8));
-    BQC_SOLVER_TRY(cusolverDnDgesvd_bufferSize(w.sol, no, no, &svd_lwork));
-    BQC_TRY(svdw.alloc(ctx, (size_t)std::max(1, svd_lwork) * 8));
-    BQC_TRY(svdinfo.alloc(ctx, sizeof(int)));
   }
   bool need_anchor = true;    // the first FP64-stage build is full
   bool last_incremental = false;
   bool confirming = false;     // a full build redoing a converged incremental iteration
-  int anchors = 0, inc_since_anchor = 0;
-  double anchor_err = INFINITY;
+  int anchors = 0, inc_since_anchor = 0, inc_stalled = 0;
+  double anchor_err = INFINITY, inc_best = INFINITY;
   std::vector<double> hev;
   // The Fock build of an iteration (C -> C_occ row-major, J, K, F) has no
   // host synchronisation in stored mode, so it is captured once per precision
@@ -341,19 +348,25 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
                                n, Ca.as<double>(), n, &zero, Sca.as<double>(), n));
       BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_T, CUBLAS_OP_N, no, no, n, &one, Cc.as<double>(),
                                n, Sca.as<double>(), n, &zero, Mo.as<double>(), no));
-      BQC_SOLVER_TRY(cusolverDnDgesvd(w.sol, 'A', 'A', no, no, Mo.as<double>(), no,
-                                      So.as<double>(), Uo.as<double>(), no, VTo.as<double>(), no,
-                                      svdw.as<double>(), svd_lwork, nullptr,
-                                      svdinfo.as<int>()));
-      int hinfo = 0;
-      BQC_CUDA_TRY(cudaMemcpyAsync(&hinfo, svdinfo.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      // R = M (M^T M)^(-1/2), the orthogonal polar factor of M (= U V^T of
+      // its SVD), from the eigen-decomposition of M^T M = V diag(lam) V^T
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_T, CUBLAS_OP_N, no, no, no, &one, Mo.as<double>(),
+                               no, Mo.as<double>(), no, &zero, Uo.as<double>(), no));
+      BQC_TRY(eigh(w, ctx, Uo.as<double>(), no, So.as<double>(), work, info, s));
+      double lam_min = 0.0;
+      BQC_CUDA_TRY(cudaMemcpyAsync(&lam_min, So.p, 8, cudaMemcpyDeviceToHost, s));
       BQC_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hinfo != 0) {
-        set_error("gesvd did not converge", __FILE__, __LINE__);
-        return BQC_E_CUDA;
-      }
-      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, no, no, no, &one, Uo.as<double>(),
-                               no, VTo.as<double>(), no, &zero, Ro.as<double>(), no));
+      // the occupied spaces of C_k and C_a nearly orthogonal in some
+      // direction: no small rank-2k difference exists, build in full instead
+      if (!(lam_min > 1e-8)) return kIncFull;
+      k_scale_cols_rsqrt<<<nblk((int64_t)no * no), 256, 0, s>>>(no, Uo.as<double>(),
+                                                                So.as<double>(), VTo.as<double>());
+      BQC_LAUNCH_CHECK();
+      // Sca (n x no, no longer needed) holds T = V diag(lam^-1/2) V^T
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_T, no, no, no, &one, VTo.as<double>(),
+                               no, Uo.as<double>(), no, &zero, Sca.as<double>(), no));
+      BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, no, no, no, &one, Mo.as<double>(),
+                               no, Sca.as<double>(), no, &zero, Ro.as<double>(), no));
       BQC_BLAS_TRY(cublasDgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, no, no, &one, Cc.as<double>(),
                                n, Ro.as<double>(), no, &zero, Ct.as<double>(), n));
       k_procrustes_pair<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, Ca.as<double>(),
@@ -417,9 +430,16 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     const bool inc_stage = inc_on && stage == BQC_PREC_FP64 && anchors < 8;
     last_incremental = inc_stage && !need_anchor;
     if (last_incremental) {
-      BQC_TRY(incremental_build());
-      ++res->builds_incremental;
-      ++inc_since_anchor;
+      const int ist = incremental_build();
+      if (ist == kIncFull) {
+        last_incremental = false;  // this iteration becomes a full build (an anchor)
+      } else {
+        BQC_TRY(ist);
+        ++res->builds_incremental;
+        ++inc_since_anchor;
+      }
+    }
+    if (last_incremental) {
     } else if (use_graph && stage >= 0 && stage < 4 && !(df->group && stage != BQC_PREC_FP64)) {
       if (!gexec[stage]) {
         cudaGraph_t graph = nullptr;
@@ -519,7 +539,21 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
         ++anchors;
         anchor_err = emax;
         inc_since_anchor = 0;
+        inc_stalled = 0;
+        inc_best = emax;
         need_anchor = false;
+      } else if (rank2) {
+        // rank-2k increments carry errors of order |C - C_a| times the mixed
+        // rounding, far below the DIIS tolerance, so one anchor serves the
+        // whole stage; re-anchor only when the DIIS error stops falling
+        // (four increments without a 30 % gain) or after 30 increments
+        if (emax < 0.7 * inc_best) {
+          inc_best = emax;
+          inc_stalled = 0;
+        } else {
+          ++inc_stalled;
+        }
+        if (inc_stalled >= 4 || inc_since_anchor >= 30) need_anchor = true;
       } else if ((emax < 100.0 * o.diis_tol && anchor_err >= 100.0 * o.diis_tol) ||
                  inc_since_anchor >= 10) {
         need_anchor = true;  // the next build is full
