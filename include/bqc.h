@@ -257,6 +257,22 @@ int bqc_jk_fp64_noalloc(const double *B_dev, int naux, int nbf, const double *C_
 int bqc_jk_host(bqc_df *df, const double *C_occ, int nocc, int prec, double *J, double *K,
                 bqc_stream_t stream);
 
+/* The Coulomb matrix of any symmetric density from the stored tensor, as the
+ * two passes over the CD-ERIs of Sec. 2.2: w_P = sum_{mu nu} B_P,mu nu D_mu nu,
+ * then J = sum_P w_P B_P.  D_dev and J_dev are device N x N, row-major (D
+ * symmetric; its lower triangle is read).  BQC_COULOMB_FP64 runs both passes
+ * with FP64 FMAs over the FP64 B; BQC_COULOMB_FF runs them on the FP32 pipe
+ * in float-float arithmetic (~2^-46 relative per term) over the float-pair
+ * copy of B that handles built with BQC_SHADOW_F16 hold (else
+ * BQC_E_UNSUPPORTED).  Each pass reads the packed B once (8 bytes per packed
+ * element); the FP64 pipe of this GPU runs 1/64 of the FP32 rate, so only the
+ * float-float passes run at the memory's speed.  Stored mode only; the first
+ * call allocates a packed-density scratch.  Async. */
+#define BQC_COULOMB_FP64 0
+#define BQC_COULOMB_FF 1
+int bqc_df_coulomb(bqc_df *df, const double *D_dev, double *J_dev, int variant,
+                   bqc_stream_t stream);
+
 /* Grouped split-FP16 Fock builds of n independent molecules (the batching
  * of launch-bound small kernels of Sec. 2.4.2 applied to Sec. 2.2's two
  * passes): J[k], K[k] of dfs[k] with C_dev[k] (device, row-major N_k x

@@ -29,6 +29,7 @@ PREC_MIXED_TF32 = 1
 PREC_MIXED_TF32X3 = 2
 PREC_MIXED_F16X3 = 3
 SHADOW_NONE, SHADOW_TF32, SHADOW_F16 = 0, 1, 2
+COULOMB_FP64, COULOMB_FF = 0, 1
 SERVE_BACKFILL, SERVE_FIFO = 0, 1
 DF_STORED, DF_DIRECT, DF_AUTO, DF_NONE = 0, 1, 2, 3
 
@@ -142,6 +143,7 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int)]),
     "bqc_jk_grouped": (ip, [ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                             ctypes.POINTER(vp), vp]),
+    "bqc_df_coulomb": (ip, [vp, vp, vp, ip, vp]),
     "bqc_wait_selftest": (ip, [vp, ctypes.c_longlong, vp]),
     "bqc_mp2": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
 }
@@ -392,6 +394,15 @@ class DF:
         check(lib().bqc_jk_host(self.h, C.ctypes.data, C.shape[1], prec, J.ctypes.data,
                                 K.ctypes.data, _stream_ptr(stream)), "bqc_jk_host")
         return J, K
+
+    def coulomb(self, D, variant: int = 0, J=None, stream=None):
+        """J[D] (N x N device tensor) of a symmetric density by the two passes
+        over B: variant COULOMB_FP64 (FP64 FMAs) or COULOMB_FF (float-float)."""
+        n = self.basis.nbf
+        J = _empty((n, n)) if J is None else J
+        check(lib().bqc_df_coulomb(self.h, _ptr(D), _ptr(J), variant, _stream_ptr(stream)),
+              "bqc_df_coulomb")
+        return J
 
     def timing(self, enable: bool = True):
         check(lib().bqc_df_timing(self.h, 1 if enable else 0), "bqc_df_timing")

@@ -106,11 +106,98 @@ __global__ void __launch_bounds__(256) k_jpass64_range(const double *__restrict_
   jpass64_cols(B, w, Pa, Pb, npair, c2, Jp + (int64_t)(y0 + blockIdx.y) * npair);
 }
 
+// (sh, sl) += (wh + wl) (bh + bl) in float-float arithmetic: the exact
+// product wh*bh (its rounding error from one FMA), the two cross terms (wl*bl
+// is below 2^-48 of the product), and a two-sum into the running pair.
+__device__ __forceinline__ void ff_acc(float &sh, float &sl, float wh, float wl, float bh,
+                                       float bl) {
+  const float p = wh * bh;
+  float e = fmaf(wh, bh, -p);
+  e = fmaf(wh, bl, e);
+  e = fmaf(wl, bh, e);
+  const float t = sh + p;
+  const float bp = t - sh;
+  const float err = (sh - (t - bp)) + (p - bp);
+  sh = t;
+  sl += err + e;
+}
+
+// out[col] = sum_{P in [Pa, Pb)} w_P B[P][col] for the columns c2, c2 + 1 of
+// a thread, from the float-pair B (one 16-byte load per P: hi0 lo0 hi1 lo1)
+// and float-pair w, accumulated in float-float: the FP32 pipe does what the
+// FP64 pipe (1/64 of its rate) would, at ~2^-46 relative per term, so the
+// pass runs at the memory's speed.
+__device__ __forceinline__ void jpass_ff_cols(const float4 *__restrict__ B2,
+                                              const float2 *__restrict__ w2, int Pa, int Pb,
+                                              int64_t npair, int64_t c2,
+                                              double *__restrict__ out) {
+  float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+  if (c2 + 1 < npair && (npair % 2 == 0)) {
+    const float4 *b = B2 + c2 / 2;
+    const int64_t st = npair / 2;
+    int P = Pa;
+    for (; P + 8 <= Pb; P += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(b + (int64_t)(P + k) * st);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 wp = __ldg(w2 + P + k);
+        ff_acc(h0, l0, wp.x, wp.y, v[k].x, v[k].y);
+        ff_acc(h1, l1, wp.x, wp.y, v[k].z, v[k].w);
+      }
+    }
+    for (; P < Pb; ++P) {
+      const float4 v = __ldg(b + (int64_t)P * st);
+      const float2 wp = __ldg(w2 + P);
+      ff_acc(h0, l0, wp.x, wp.y, v.x, v.y);
+      ff_acc(h1, l1, wp.x, wp.y, v.z, v.w);
+    }
+    out[c2] = (double)h0 + (double)l0;
+    out[c2 + 1] = (double)h1 + (double)l1;
+  } else {
+    const float2 *b = reinterpret_cast<const float2 *>(B2);
+    for (int P = Pa; P < Pb; ++P) {
+      const float2 wp = __ldg(w2 + P);
+      const float2 v0 = __ldg(b + (int64_t)P * npair + c2);
+      ff_acc(h0, l0, wp.x, wp.y, v0.x, v0.y);
+      if (c2 + 1 < npair) {
+        const float2 v1 = __ldg(b + (int64_t)P * npair + c2 + 1);
+        ff_acc(h1, l1, wp.x, wp.y, v1.x, v1.y);
+      }
+    }
+    out[c2] = (double)h0 + (double)l0;
+    if (c2 + 1 < npair) out[c2 + 1] = (double)h1 + (double)l1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_jpass_ff_range(const float4 *__restrict__ B2,
+                                                        const float2 *__restrict__ w2, int P0,
+                                                        int P1, int64_t npair, int y0,
+                                                        double *__restrict__ Jp) {
+  const int64_t c2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (c2 >= npair) return;
+  const int per = (P1 - P0 + gridDim.y - 1) / gridDim.y;
+  const int Pa = P0 + blockIdx.y * per, Pb = min(P1, Pa + per);
+  jpass_ff_cols(B2, w2, Pa, Pb, npair, c2, Jp + (int64_t)(y0 + blockIdx.y) * npair);
+}
+
+// B (FP64) -> float pairs (hi, lo), hi = fl(B), lo = fl(B - hi).
+__global__ void k_split_ff(const double *__restrict__ B, int64_t count, float2 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double d = B[i];
+  const float h = (float)d;
+  out[i] = make_float2(h, (float)(d - (double)h));
+}
+
 // Grouped J pass of independent problems in one launch: problem k owns the
 // blocks [off[k], off[k + 1]) as xb[k] column blocks times sp[k] aux chunks.
 struct JGroup {
   const double *B[kMaxGroup];
   const double *w[kMaxGroup];
+  const float4 *B2[kMaxGroup];  // float-pair B and w (ff variant)
+  const float2 *w2[kMaxGroup];
   double *Jp[kMaxGroup];
   double *J[kMaxGroup];
   int64_t npair[kMaxGroup];
@@ -119,6 +206,7 @@ struct JGroup {
   int nprob;
 };
 
+template <bool FF>
 __global__ void __launch_bounds__(256) k_jpass64_grp(const __grid_constant__ JGroup g) {
   const int bid = blockIdx.x;
   int k = 0;
@@ -129,7 +217,10 @@ __global__ void __launch_bounds__(256) k_jpass64_grp(const __grid_constant__ JGr
   if (c2 >= npair) return;
   const int per = (g.naux[k] + g.sp[k] - 1) / g.sp[k];
   const int Pa = y * per, Pb = min(g.naux[k], Pa + per);
-  jpass64_cols(g.B[k], g.w[k], Pa, Pb, npair, c2, g.Jp[k] + (int64_t)y * npair);
+  if (FF)
+    jpass_ff_cols(g.B2[k], g.w2[k], Pa, Pb, npair, c2, g.Jp[k] + (int64_t)y * npair);
+  else
+    jpass64_cols(g.B[k], g.w[k], Pa, Pb, npair, c2, g.Jp[k] + (int64_t)y * npair);
 }
 
 __device__ __forceinline__ void unpack_jsum_one(const double *Jp, int nsplit, int64_t npair, int n,
@@ -215,6 +306,70 @@ __global__ void __launch_bounds__(256) k_bdot(const double *__restrict__ B, int6
   if (threadIdx.x == 0) w[blockIdx.x] = red[0];
 }
 
+// The packed, off-diagonal-doubled density as float pairs (hi, lo).
+__global__ void k_pack_sym2_ff(const double *__restrict__ D, int n, float2 *__restrict__ D2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * (n + 1) / 2) return;
+  int mu = (int)((sqrt(8.0 * (double)i + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(mu + 1) * (mu + 2) / 2 <= i) ++mu;
+  while ((int64_t)mu * (mu + 1) / 2 > i) --mu;
+  const int nu = (int)(i - (int64_t)mu * (mu + 1) / 2);
+  const double v = (mu == nu ? 1.0 : 2.0) * D[(int64_t)mu * n + nu];
+  const float h = (float)v;
+  D2[i] = make_float2(h, (float)(v - (double)h));
+}
+
+// w[P] = sum_c B[P][c] D2[c] from the float pairs of B and D2 in float-float
+// arithmetic (one block per P; the block's partial pairs summed in FP64);
+// also w as float pairs for the J pass.
+__global__ void __launch_bounds__(256) k_bdot_ff(const float2 *__restrict__ B2, int64_t npair,
+                                                 const float2 *__restrict__ D2, double *w,
+                                                 float2 *w2) {
+  const float2 *b = B2 + (int64_t)blockIdx.x * npair;
+  float h = 0.0f, l = 0.0f;
+  if (npair % 2 == 0) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(b);
+    const float4 *d4 = reinterpret_cast<const float4 *>(D2);
+    for (int64_t c = threadIdx.x; c < npair / 2; c += blockDim.x) {
+      const float4 x = __ldg(b4 + c), d = __ldg(d4 + c);
+      ff_acc(h, l, d.x, d.y, x.x, x.y);
+      ff_acc(h, l, d.z, d.w, x.z, x.w);
+    }
+  } else {
+    for (int64_t c = threadIdx.x; c < npair; c += blockDim.x) {
+      const float2 x = __ldg(b + c), d = __ldg(D2 + c);
+      ff_acc(h, l, d.x, d.y, x.x, x.y);
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = (double)h + (double)l;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = red[0];
+    w[blockIdx.x] = v;
+    const float fh = (float)v;
+    w2[blockIdx.x] = make_float2(fh, (float)(v - (double)fh));
+  }
+}
+
+int jff_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s) {
+  if (df->mode != BQC_DF_STORED || !df->B2f.p || !df->w2f.p) return BQC_E_INVALID;
+  const int n = df->basis->nbf;
+  float2 *d2 = reinterpret_cast<float2 *>(D2);  // npair doubles hold npair float pairs
+  k_pack_sym2_ff<<<(unsigned)((df->npair + 255) / 256), 256, 0, s>>>(D, n, d2);
+  BQC_LAUNCH_CHECK();
+  k_bdot_ff<<<(unsigned)df->naux_loc, 256, 0, s>>>(df->B2f.as<float2>(), df->npair, d2,
+                                                   df->w.as<double>(), df->w2f.as<float2>());
+  BQC_LAUNCH_CHECK();
+  const int sp = jpass_split(df->npair, df->naux_loc);
+  BQC_TRY(jpass_ff_range(df, 0, df->naux_loc, 0, s));
+  return jpass_unpack(df, sp, J, s);
+}
+
 int jfp64_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s) {
   if (df->mode != BQC_DF_STORED || !df->B64.p) return BQC_E_INVALID;
   const int n = df->basis->nbf;
@@ -236,6 +391,27 @@ int jpass_fp64_range(Df *df, int P0, int P1, int y0, cudaStream_t s) {
   return BQC_OK;
 }
 
+int jpass_ff_setup(Df *df, cudaStream_t s) {
+  const int64_t count = (int64_t)df->naux_loc * df->npair;
+  BQC_TRY(df->B2f.alloc(df->ctx, (size_t)count * 8));
+  BQC_TRY(df->w2f.alloc(df->ctx, (size_t)df->naux_loc * 8));
+  k_split_ff<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(df->B64.as<double>(), count,
+                                                             df->B2f.as<float2>());
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
+int jpass_ff_range(Df *df, int P0, int P1, int y0, cudaStream_t s) {
+  const int64_t npair = df->npair;
+  const int sp = jpass_split(npair, P1 - P0);
+  if (!df->B2f.p || !df->w2f.p || df->Jp.n < (size_t)(y0 + sp) * npair * 8)
+    return BQC_E_INVALID;
+  k_jpass_ff_range<<<dim3((unsigned)((npair / 2 + 256) / 256), (unsigned)sp), 256, 0, s>>>(
+      df->B2f.as<float4>(), df->w2f.as<float2>(), P0, P1, npair, y0, df->Jp.as<double>());
+  BQC_LAUNCH_CHECK();
+  return BQC_OK;
+}
+
 int jpass_unpack(Df *df, int nslice, double *J, cudaStream_t s) {
   const int n = df->basis->nbf;
   k_unpack_jsum<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(df->Jp.as<double>(),
@@ -249,6 +425,7 @@ int group_jpass(Df *const *dfs, double *const *J, int n, cudaStream_t s) {
   JGroup g;
   std::memset(&g, 0, sizeof(g));
   int blocks = 0;
+  bool ff = true;
   int64_t nn_max = 0;
   for (int k = 0; k < n; ++k) {
     Df *df = dfs[k];
@@ -259,6 +436,9 @@ int group_jpass(Df *const *dfs, double *const *J, int n, cudaStream_t s) {
     if (df->Jp.n < (size_t)sp * npair * 8) return BQC_E_INVALID;
     g.B[k] = df->B64.as<double>();
     g.w[k] = df->w.as<double>();
+    g.B2[k] = df->B2f.as<float4>();
+    g.w2[k] = df->w2f.as<float2>();
+    ff = ff && df->B2f.p && df->w2f.p;
     g.Jp[k] = df->Jp.as<double>();
     g.J[k] = J[k];
     g.npair[k] = npair;
@@ -272,7 +452,10 @@ int group_jpass(Df *const *dfs, double *const *J, int n, cudaStream_t s) {
   }
   g.off[n] = blocks;
   g.nprob = n;
-  k_jpass64_grp<<<(unsigned)blocks, 256, 0, s>>>(g);
+  if (ff)
+    k_jpass64_grp<true><<<(unsigned)blocks, 256, 0, s>>>(g);
+  else
+    k_jpass64_grp<false><<<(unsigned)blocks, 256, 0, s>>>(g);
   BQC_LAUNCH_CHECK();
   k_unpack_jsum_grp<<<dim3((unsigned)((nn_max + 255) / 256), (unsigned)n), 256, 0, s>>>(g);
   BQC_LAUNCH_CHECK();
@@ -335,6 +518,14 @@ size_t df_stored_bytes(int n, int naux, int nocc, int shadow) {
   b += (size_t)jpass_split((int64_t)npair, naux) * npair * 8 + (size_t)naux * 8 * 2;
   if (shadow == BQC_SHADOW_TF32 || shadow == BQC_SHADOW_F16)
     b += mixed_workspace_bytes(n, naux, nocc, shadow);
+  if (shadow == BQC_SHADOW_F16) {  // float-pair B and w of the J pass, the pieces' J partials
+    b += (size_t)naux * npair * 8 + (size_t)naux * 8;
+    const int np = std::min(kJPieces, std::max(naux, 1));
+    for (int k = 0; k < np; ++k)
+      b += (size_t)jpass_split((int64_t)npair, (int)((int64_t)naux * (k + 1) / np) -
+                                                   (int)((int64_t)naux * k / np)) *
+           npair * 8;
+  }
   return b;
 }
 
@@ -343,6 +534,29 @@ size_t df_stored_bytes(int n, int naux, int nocc, int shadow) {
 using namespace bqc;
 
 extern "C" {
+
+int bqc_df_coulomb(bqc_df *df, const double *D_dev, double *J_dev, int variant,
+                   bqc_stream_t stream) {
+  if (!df || !D_dev || !J_dev || (variant != BQC_COULOMB_FP64 && variant != BQC_COULOMB_FF))
+    return BQC_E_INVALID;
+  if (df->mode != BQC_DF_STORED || !df->B64.p) {
+    set_error("bqc_df_coulomb needs a stored handle", __FILE__, __LINE__);
+    return BQC_E_UNSUPPORTED;
+  }
+  if (variant == BQC_COULOMB_FF && !df->B2f.p) {
+    set_error("the float-float Coulomb pass needs a handle built with BQC_SHADOW_F16",
+              __FILE__, __LINE__);
+    return BQC_E_UNSUPPORTED;
+  }
+  BQC_CUDA_TRY(cudaSetDevice(df->ctx->device));
+  if (df->D2.n < (size_t)df->npair * 8) BQC_TRY(df->D2.alloc(df->ctx, (size_t)df->npair * 8));
+  const int need = jpass_split(df->npair, df->naux_loc);
+  if (df->Jp.n < (size_t)need * df->npair * 8)
+    BQC_TRY(df->Jp.alloc(df->ctx, (size_t)need * df->npair * 8));
+  cudaStream_t s = (cudaStream_t)stream;
+  return variant == BQC_COULOMB_FF ? jff_of_density(df, D_dev, df->D2.as<double>(), J_dev, s)
+                                   : jfp64_of_density(df, D_dev, df->D2.as<double>(), J_dev, s);
+}
 
 int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
                  bqc_stream_t stream, bqc_df **out) {

@@ -43,6 +43,10 @@ struct Df {
   DBuf X64;    // Naux x N x nocc, FP64
   DBuf Jp;     // Npair FP64 (packed J)
   DBuf w;      // Naux FP64: w_P = B_P : D
+  // float-pair copy of B for the J pass of the split-FP16 build on the FP32
+  // pipe: [P][Npair][2] = (hi, lo), hi = fl(B), lo = fl(B - hi); and w as
+  // float pairs [Naux][2]
+  DBuf B2f, w2f;
   DBuf host_io;
   // mixed precision (TF32 tensor cores)
   DBuf B32;    // Naux x N x ld, TF32 hi part of B, full square (MMA A operand)
@@ -94,7 +98,8 @@ struct Df {
     if (side) cudaStreamDestroy(side);
   }
   size_t device_bytes() const {
-    return L.n + Vdiag.n + B64.n + X64.n + Jp.n + w.n + host_io.n + B32.n + X32.n + Ct32.n +
+    return L.n + Vdiag.n + B64.n + B2f.n + w2f.n + X64.n + Jp.n + w.n + host_io.n + B32.n +
+           X32.n + Ct32.n +
            wpart.n + Kpart.n + raw.n + Linv.n + Xraw.n + gamma.n + D2.n +
            plan.d_pairs_sorted.n + plan.d_qpair_sorted.n + plan.d_qaux.n + plan.d_prefix.n +
            plan.d_qpair.n +
@@ -118,10 +123,16 @@ int jpass_fp64(Df *df, double *J, cudaStream_t s);
 // partial slices starting at y0, then the sum of nslice slices into J.
 int jpass_fp64_range(Df *df, int P0, int P1, int y0, cudaStream_t s);
 int jpass_unpack(Df *df, int nslice, double *J, cudaStream_t s);
+// The same J partials from the float-pair B and w (df->B2f, df->w2f) in
+// float-float arithmetic on the FP32 pipe; jpass_ff_setup builds B2f.
+int jpass_ff_setup(Df *df, cudaStream_t s);
+int jpass_ff_range(Df *df, int P0, int P1, int y0, cudaStream_t s);
 int jpass_split(int64_t npair, int naux);
 // J[D] = sum_P (B_P : D) B_P in FP64 over the stored FP64 B for a symmetric
 // N x N matrix D (any sign), D2 an Npair scratch.
 int jfp64_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s);
+// The same on the FP32 pipe from the float-pair B (float-float arithmetic).
+int jff_of_density(Df *df, const double *D, double *D2, double *J, cudaStream_t s);
 int direct_setup(Df *df, cudaStream_t s);
 size_t direct_mixed_bytes(int n, int naux, int nocc, int bs);
 int direct_mixed_setup(Df *df, const double *Linv, int bs, cudaStream_t s);

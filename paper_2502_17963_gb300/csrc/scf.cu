@@ -336,7 +336,12 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     // mode): J is linear in the density, so no factorisation and no
     // cancellation between the two signed parts
     const bool jexact = df->mode == BQC_DF_STORED && df->B64.p;
-    if (jexact) BQC_TRY(jfp64_of_density(df, t1.as<double>(), D2p.as<double>(), Jx.as<double>(), s));
+    if (jexact) {
+      if (df->B2f.p)
+        BQC_TRY(jff_of_density(df, t1.as<double>(), D2p.as<double>(), Jx.as<double>(), s));
+      else
+        BQC_TRY(jfp64_of_density(df, t1.as<double>(), D2p.as<double>(), Jx.as<double>(), s));
+    }
     if (rank2) {
       // Exchange part as a rank-2k update: rotate the current occupied
       // orbitals Ck onto the anchor's Ca (orthogonal Procrustes in the S

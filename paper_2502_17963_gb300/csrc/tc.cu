@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, xpass_min_blocks(XN))
 // w[P] = sum over partials and mu of wpart[k][P*N + mu] (FP64); also fp32 w.
 // One 256-thread block per P.
 __device__ __forceinline__ void wreduce_one(const float *wpart, int64_t rows, int nparts, int n,
-                                            double *w, float *w32, int P) {
+                                            double *w, float *w32, float2 *w2, int P) {
   double s = 0.0;
   for (int g = 0; g < nparts; ++g)
     for (int m = threadIdx.x; m < n; m += blockDim.x) s += wpart[g * rows + (int64_t)P * n + m];
@@ -514,12 +514,17 @@ __device__ __forceinline__ void wreduce_one(const float *wpart, int64_t rows, in
   if (threadIdx.x == 0) {
     w[P] = red[0];
     w32[P] = (float)red[0];
+    if (w2) {  // float pair (hi, lo) for the float-float J pass
+      const float h = (float)red[0];
+      w2[P] = make_float2(h, (float)(red[0] - (double)h));
+    }
   }
 }
 
 __global__ void __launch_bounds__(256) k_wreduce(const float *wpart, int64_t rows, int nparts,
-                                                 int n, double *w, float *w32, int P0) {
-  wreduce_one(wpart, rows, nparts, n, w, w32, P0 + blockIdx.x);
+                                                 int n, double *w, float *w32, float2 *w2,
+                                                 int P0) {
+  wreduce_one(wpart, rows, nparts, n, w, w32, w2, P0 + blockIdx.x);
 }
 
 // ---------------------------------------------------------------- SYRK ---
@@ -1717,6 +1722,9 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   std::memcpy(&maxsq, &hb, 4);
   // |B row| <= |Bh row| / (1 - 2^-11); the factor also covers the float sums
   ms->rownorm = std::sqrt((double)maxsq) / (double)sB * (1.0 + 1.0 / 256.0);
+  // float-pair B for the J pass on the FP32 pipe (8 bytes per packed
+  // element, like the FP64 B it is split from)
+  BQC_TRY(jpass_ff_setup(df, s));
   {  // room for the J partials of the pieces
     const int np = std::min(kJPieces, naux);
     int slices = 0;
@@ -1898,7 +1906,10 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
                       grid, s));
   if (w_out) {
     k_wreduce<<<(unsigned)(P1 - P0), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
-                                                   w_out, ms->w32.as<float>(), P0);
+                                                   w_out, ms->w32.as<float>(),
+                                                   w_out == df->w.as<double>() ? df->w2f.as<float2>()
+                                                                               : nullptr,
+                                                   P0);
     BQC_LAUNCH_CHECK();
   }
   return BQC_OK;
@@ -1999,6 +2010,7 @@ struct WredGroup {
   const float *wpart[kMaxGroup];
   double *w[kMaxGroup];
   float *w32[kMaxGroup];
+  float2 *w2[kMaxGroup];
   int64_t rows[kMaxGroup];
   int nparts[kMaxGroup], n[kMaxGroup], naux[kMaxGroup];
 };
@@ -2006,7 +2018,7 @@ struct WredGroup {
 __global__ void __launch_bounds__(256) k_wreduce_grp(const __grid_constant__ WredGroup g) {
   const int k = blockIdx.y;
   if ((int)blockIdx.x >= g.naux[k]) return;
-  wreduce_one(g.wpart[k], g.rows[k], g.nparts[k], g.n[k], g.w[k], g.w32[k], blockIdx.x);
+  wreduce_one(g.wpart[k], g.rows[k], g.nparts[k], g.n[k], g.w[k], g.w32[k], g.w2[k], blockIdx.x);
 }
 
 struct SyRedGroup {
@@ -2096,6 +2108,7 @@ int group_xpass(Df *const *dfs, int n, cudaStream_t s) {
     wr->wpart[k] = ms->wpart.as<float>();
     wr->w[k] = df->w.as<double>();
     wr->w32[k] = ms->w32.as<float>();
+    wr->w2[k] = df->w2f.as<float2>();
     wr->rows[k] = p.rows;
     wr->nparts[k] = 2 * m.ncg;
     wr->n[k] = nb;
@@ -2236,7 +2249,10 @@ int jk_mixed_stored(Df *df, const double *C, int prec, double *J, double *K, cud
     for (int k = 0; k < np; ++k) {
       const int Pa = (int)((int64_t)naux * k / np), Pb = (int)((int64_t)naux * (k + 1) / np);
       BQC_CUDA_TRY(cudaStreamWaitEvent(js, df->piece[k], 0));
-      BQC_TRY(jpass_fp64_range(df, Pa, Pb, y, js));
+      if (df->B2f.p)
+        BQC_TRY(jpass_ff_range(df, Pa, Pb, y, js));
+      else
+        BQC_TRY(jpass_fp64_range(df, Pa, Pb, y, js));
       y += jpass_split(df->npair, Pb - Pa);
     }
     BQC_TRY(jpass_unpack(df, y, J, js));
