@@ -745,6 +745,32 @@ def main():
                         "(staged_scf)",
                 "speedup_mixed_over_fp64": fms / ms_per_step}
 
+    # the Coulomb matrix alone by the two passes over B (w = B.D, J = sum w_P
+    # B_P): FP64 FMAs vs float-float on the FP32 pipe, on achieved HBM GB/s
+    coul = None
+    if args.prec == "f16x3":
+        Dm = C @ C.T
+        Jc = torch.empty_like(J)
+        coul = {}
+        for label, var in (("fp64", bqc.COULOMB_FP64), ("float_float", bqc.COULOMB_FF)):
+            df.coulomb(Dm, var, Jc)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(5):
+                df.coulomb(Dm, var, Jc)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1) / 5
+            cbytes = 2.0 * basis.naux * n * (n + 1) / 2 * 8  # two reads of the packed B
+            coul[label] = {"ms": cms, "gbs": cbytes / (cms * 1e-3) / 1e9,
+                           "frac_of_hbm": cbytes / (cms * 1e-3) / 1e9 / peaks()[0]["hbm_gbs"]}
+        coul["bytes_per_call"] = 2.0 * basis.naux * n * (n + 1) / 2 * 8
+        coul["note"] = ("bqc_df_coulomb at the benchmark density: w = B.D then J = sum_P w_P B_P, "
+                        "each pass one read of the packed B (8 bytes per element: FP64, or the "
+                        "float-pair copy); CUDA events, mean of 5, inputs larger than L2")
+
     # end to end through the C ABI with host buffers (H2D of C_occ, D2H of J, K)
     e2e = None
     if not args.no_e2e:
@@ -804,6 +830,7 @@ def main():
     jbytes = naux * n * (n + 1) / 2 * 8  # J pass: one read of the packed FP64 B
     kflops = n * n * naux * no           # SYRK half (algorithmic; 3 products issued)
     extra = {
+        "coulomb": coul,
         "phases_ms": {"x_pass": ph_mean[0], "j_pass": ph_mean[1], "k_syrk": ph_mean[2],
                       "prep": ph_mean[3]},
         "j_pass_gbs_beside_syrk": jbytes / (ph_mean[1] * 1e-3) / 1e9,

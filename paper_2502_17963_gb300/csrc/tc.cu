@@ -369,8 +369,11 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
           for (int i = 0; i < 16; ++i) a[i] = acc[(c + i) % AREG];
         }
       };
+      // tcgen05.ld is warp-collective: every lane reads the accumulators
+      // (acc16), and only the lanes of valid rows store
       const int64_t row = m0 + q * 32 + lane;
-      if (KIND == kKindF16 && ok && row < row_end) {
+      const bool act = ok && row < row_end;
+      if (KIND == kKindF16) {
         // scaled X split into FP16 hi + lo (each rounded to nearest), and the
         // fused w partial sum_i X[row][i] C[mu][i] of the unscaled X
         const float xo = p.scale->x_out, xu = p.scale->x_unscale;
@@ -386,7 +389,7 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
             float a16[16];
             acc16(c16, a16);
 #pragma unroll
-            for (int e = 0; e < 16; e += 8) {
+            for (int e = 0; e < 16 && act; e += 8) {
               const int c = c16 + e;
               const float *av = a16 + e;
               const float4 ca = *reinterpret_cast<const float4 *>(cr + c);
@@ -411,9 +414,9 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
             }
           }
         }
-        p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum * xu;
+        if (act) p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum * xu;
       }
-      if (KIND == kKindTF32 && EPI == 0 && ok && row < row_end) {
+      if (KIND == kKindTF32 && EPI == 0) {
         const int mu = (int)(row % p.n);
         const int col = cg * T.xn + h * half;
         float *xh = p.Xh + row * p.ldx + col;
@@ -426,7 +429,7 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
             float a16[16];
             acc16(c16, a16);
 #pragma unroll
-            for (int e = 0; e < 16; e += 4) {
+            for (int e = 0; e < 16 && act; e += 4) {
               const int c = c16 + e;
               const float *av = a16 + e;
               const float4 cc = *reinterpret_cast<const float4 *>(cr + c);
@@ -450,9 +453,10 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
             }
           }
         }
-        p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum;
+        if (act) p.wpart[(int64_t)(2 * cg + h) * p.wstride + row] = wsum;
       }
-      if (KIND == kKindTF32 && EPI == 1 && ok && row < row_end && (int)(row % p.bk) < p.bkv) {
+      if (KIND == kKindTF32 && EPI == 1) {
+        const bool act1 = act && (int)(row % p.bk) < p.bkv;
         // consecutive lanes hold consecutive q of one mu: coalesced per column
         const int64_t mu = row / p.bk, qq = p.q0 + row % p.bk;
         const int col = cg * T.xn + h * half;
@@ -464,7 +468,7 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
             float a16[16];
             acc16(c16, a16);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < 16 && act1; ++e) {
               const int c = c16 + e;
               const float hv = tf32r(a16[e]);
               p.Xh[base + (int64_t)c * step] = hv;
