@@ -48,8 +48,10 @@ def test_grouped_equals_single(gpu_ctx, bqc, names):
     torch.cuda.synchronize()
     for (J1, K1), J2, K2, nm in zip(ref, Js, Ks, names):
         assert torch.equal(K1, K2), nm
+        # J: float-float sums (~2^-46 per term) over a different aux
+        # chunking; J cancels by up to ~100x against its terms here
         ja = float(J1.abs().max())
-        assert float((J1 - J2).abs().max()) <= 1e-13 * ja, nm
+        assert float((J1 - J2).abs().max()) <= 1e-11 * ja, nm
         assert torch.equal(J2, J2.T) and torch.equal(K2, K2.T)
     # repeat: the grouped build leaves nothing behind that changes the next
     Js2, Ks2 = bqc.jk_grouped(dfs, Cs)
