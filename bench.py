@@ -487,7 +487,10 @@ def staged_scf_check(bqc, ctx, df, torch, prec):
                        "fp64_stage": "anchored incremental (final build full FP64)",
                        "converged": rs["converged"], "diis_err": rs["diis_err"],
                        "switch_rule": rs["switch_rule"], "switch_err": rs["switch_err"],
-                       "stage_tol": 1e-5},
+                       "stage_tol": 1e-5,
+                       # per build: precision (3 split FP16, 2 split TF32, 0 full FP64,
+                       # -1 incremental FP64) and the DIIS error max|e| after it
+                       "history": [[int(p), float(f"{e:.3g}")] for p, e, _ in rs["history"]]},
             "fp64_scf": {"wall_s": t64, "fock_builds": len(r64["history"]),
                          "converged": r64["converged"], "diis_err": r64["diis_err"]},
             "protocol": "core-Hamiltonian guess, DIIS(8), converged at max|e| < 1e-8 and "
