@@ -849,11 +849,16 @@ def main():
         "fp64": fp64,
         "tf32_single_pass": tf1,
     }
+    # kernels of one build: split-FP16 = C split (3), four X-pass pieces with
+    # their w reductions (8), four float-float J pieces and the unpack (5), the
+    # SYRK and its reduction (2); split-TF32 = C split, X pass, w, J, unpack,
+    # SYRK, reduction
+    launches_per_build = 18 if args.prec == "f16x3" else 7
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": config(mol, "mixed_" + args.prec), "roofline": roofline,
-            "gpu_launches": 7 * args.steps, "clocks": clk, "e2e": e2e}
+            "gpu_launches": launches_per_build * args.steps, "clocks": clk, "e2e": e2e}
     line.update(extra)
     if not args.no_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(mol)
