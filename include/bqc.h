@@ -53,7 +53,8 @@ enum {
   BQC_E_TIMEOUT = -6,       /* a bounded device or host wait ran out        */
   BQC_E_DEVICE_FLAG = -7,   /* a kernel's own bounds check tripped          */
   BQC_E_NOT_READY = -8,     /* serving: result not available yet            */
-  BQC_E_UNSUPPORTED = -9    /* angular momentum / size the library lacks    */
+  BQC_E_UNSUPPORTED = -9,   /* angular momentum / size the library lacks    */
+  BQC_E_CANCELLED = -10     /* serving: the request was cancelled           */
 };
 
 /* Precision of the Fock build (the X = B C and K contractions, the B.D
@@ -471,6 +472,13 @@ int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out)
 int bqc_serve_submit(bqc_server *srv, const bqc_request *req, uint64_t *ticket);
 /* BQC_OK with the result once done, BQC_E_NOT_READY before. */
 int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res);
+/* Cancels a request.  A queued one completes at once with status
+ * BQC_E_CANCELLED; a running one stops at its next step boundary (before the
+ * DF build, before the SCF, or between SCF iterations, never with work of
+ * its own in flight) and completes with BQC_E_CANCELLED, its memory
+ * returned to the ledger; one already done is left as it is.  BQC_OK, or
+ * BQC_E_INVALID for an unknown ticket. */
+int bqc_serve_cancel(bqc_server *srv, uint64_t ticket);
 /* Wait (at most timeout_s seconds, <= 0 = no limit) until all submitted
  * requests are done; BQC_E_TIMEOUT otherwise. */
 int bqc_serve_drain(bqc_server *srv, double timeout_s);

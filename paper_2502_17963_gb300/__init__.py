@@ -24,6 +24,7 @@ BQC_E_INVALID = -1
 BQC_E_NOT_CONVERGED = -4
 BQC_E_NOT_READY = -8
 BQC_E_UNSUPPORTED = -9
+BQC_E_CANCELLED = -10
 PREC_FP64 = 0
 PREC_MIXED_TF32 = 1
 PREC_MIXED_TF32X3 = 2
@@ -137,6 +138,7 @@ _SIGS = {
     "bqc_serve_submit": (ip, [vp, ctypes.POINTER(bqc_request), ctypes.POINTER(ctypes.c_uint64)]),
     "bqc_serve_poll": (ip, [vp, ctypes.c_uint64, ctypes.POINTER(bqc_serve_result)]),
     "bqc_serve_drain": (ip, [vp, dp]),
+    "bqc_serve_cancel": (ip, [vp, ctypes.c_uint64]),
     "bqc_serve_destroy": (ip, [vp]),
     "bqc_serve_footprint": (ctypes.c_size_t, [ip, ip, ip, ip]),
     "bqc_serve_group_stats": (ip, [vp, ctypes.POINTER(ctypes.c_uint64),
@@ -508,6 +510,10 @@ class Server:
         return dict(status=r.status, energy=r.energy, diis_err=r.diis_err,
                     iterations=r.iterations, nbf=r.nbf, t_submit=r.t_submit, t_admit=r.t_admit,
                     t_done=r.t_done, iterations_mixed=r.iterations_mixed, priority=r.priority)
+
+    def cancel(self, ticket: int):
+        """Cancels a queued or running request (bqc_serve_cancel)."""
+        check(lib().bqc_serve_cancel(self.h, ticket), "bqc_serve_cancel")
 
     def drain(self, timeout_s: float = 0.0):
         check(lib().bqc_serve_drain(self.h, timeout_s), "bqc_serve_drain")

@@ -15,6 +15,13 @@
 
 namespace bqc {
 
+// Cancellation flag of the request the calling thread is solving (serving),
+// read by the SCF between iterations; null outside the server.
+extern thread_local const std::atomic<int> *tl_cancel;
+inline bool cancel_requested() {
+  return tl_cancel && tl_cancel->load(std::memory_order_relaxed) != 0;
+}
+
 // ------------------------------------------------------------ errors ----
 
 void set_error(const char *what, const char *file, int line);

@@ -14,6 +14,8 @@
 
 namespace bqc {
 
+thread_local const std::atomic<int> *tl_cancel = nullptr;
+
 static thread_local char g_err[512] = "";
 
 void set_error(const char *what, const char *file, int line) {
@@ -202,6 +204,7 @@ const char *bqc_strerror(int status) {
     case BQC_E_DEVICE_FLAG: return "device-side check tripped";
     case BQC_E_NOT_READY: return "not ready";
     case BQC_E_UNSUPPORTED: return "unsupported (angular momentum or size)";
+    case BQC_E_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }

@@ -432,6 +432,10 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   const bool use_graph = df->mode == BQC_DF_STORED && !df->timing && s != nullptr;
   auto graph_free = [&]() { graphs.clear(); };
   for (it = 1; it <= o.max_iter; ++it) {
+    if (cancel_requested()) {  // between iterations: nothing of ours in flight
+      BQC_CUDA_TRY(cudaStreamSynchronize(s));
+      return BQC_E_CANCELLED;
+    }
     const bool inc_stage = inc_on && stage == BQC_PREC_FP64 && anchors < 8;
     last_incremental = inc_stage && !need_anchor;
     if (last_incremental) {

@@ -133,6 +133,8 @@ struct Request {
   uint64_t release_mark = 0;      // srv->releases when it was requeued
   double t_submit = 0.0;
   bool done = false;
+  bool running = false;
+  std::atomic<int> cancel{0};
   bqc_serve_result res{};
 };
 
@@ -196,7 +198,10 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
   }
   bqc_basis *basis = nullptr;
   bqc_df *df = nullptr;
-  int st = bqc_basis_load(srv->ctx, (int)r->Z.size(), r->Z.data(), r->xyz.data(), sh[0].data(),
+  tl_cancel = &r->cancel;
+  int st = cancel_requested() ? BQC_E_CANCELLED : BQC_OK;
+  if (st == BQC_OK)
+    st = bqc_basis_load(srv->ctx, (int)r->Z.size(), r->Z.data(), r->xyz.data(), sh[0].data(),
                           (int)sh[0].size(), sh[1].data(), (int)sh[1].size(), &basis);
   bqc_scf_result res{};
   if (st == BQC_OK) {
@@ -208,6 +213,7 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
     o.hbm_limit = 0;
     st = bqc_df_build(srv->ctx, basis, &o, (bqc_stream_t)s, &df);
   }
+  if (st == BQC_OK && cancel_requested()) st = BQC_E_CANCELLED;
   if (st == BQC_OK && srv->group) df->group = srv->group;
   if (st == BQC_OK) {
     bqc_scf_opts so = srv->opts.scf;
@@ -217,6 +223,7 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
   // the stream is idle now: free without the device-wide synchronisation of
   // the public destroy calls, which would stall the other slots
   cudaStreamSynchronize(s);
+  tl_cancel = nullptr;
   delete df;
   delete basis;
   r->res.status = st;
@@ -429,6 +436,33 @@ int bqc_serve_poll(bqc_server *srv, uint64_t ticket, bqc_serve_result *res) {
   if (it == srv->reqs.end()) return BQC_E_INVALID;
   if (!it->second->done) return BQC_E_NOT_READY;
   *res = it->second->res;
+  return BQC_OK;
+}
+
+int bqc_serve_cancel(bqc_server *srv, uint64_t ticket) {
+  if (!srv) return BQC_E_INVALID;
+  bool finished_now = false;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return BQC_E_INVALID;
+    Request *r = it->second.get();
+    if (r->done) return BQC_OK;
+    r->cancel.store(1, std::memory_order_relaxed);
+    auto q = std::find(srv->queue.begin(), srv->queue.end(), ticket);
+    if (q != srv->queue.end()) {  // still queued: complete it now
+      srv->queue.erase(q);
+      r->res.status = BQC_E_CANCELLED;
+      r->res.t_done = srv->now();
+      r->done = true;
+      --srv->pending;
+      finished_now = true;
+    }
+  }
+  if (finished_now) {
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+  }
   return BQC_OK;
 }
 

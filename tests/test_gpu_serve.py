@@ -134,3 +134,29 @@ def test_backfill_admission_and_priority(gpu_ctx, bqc, policy):
     else:
         assert r3["t_admit"] >= r2["t_admit"]
         assert r3["priority"] == r1["priority"] == r2["priority"]
+
+
+def test_cancel_queued_and_running(gpu_ctx, bqc):
+    """A queued request cancelled completes at once with BQC_E_CANCELLED; a
+    running one stops at its next step boundary with the same status; the
+    server keeps serving, and a done request is left as it is."""
+    import time
+    srv = bqc.Server(gpu_ctx, max_slots=1, prec=bqc.PREC_FP64, hbm_budget=4 << 30)
+    t_run = srv.submit(workload.water_cluster(16))
+    t_q = srv.submit(workload.molecule_for("w2"))
+    t_ok = srv.submit(workload.molecule_for("h2o"))
+    srv.cancel(t_q)
+    r_q = srv.poll(t_q)
+    assert r_q is not None and r_q["status"] == bqc.BQC_E_CANCELLED
+    time.sleep(0.3)  # the first solve is admitted (one slot) and running
+    srv.cancel(t_run)
+    srv.drain(300)
+    r_run, r_ok = srv.poll(t_run), srv.poll(t_ok)
+    assert r_run["status"] == bqc.BQC_E_CANCELLED, r_run
+    assert r_ok["status"] == 0, r_ok
+    srv.cancel(t_ok)  # already done: unchanged
+    assert srv.poll(t_ok)["status"] == 0
+    with pytest.raises(bqc.BqcError) as e:
+        srv.cancel(123456789)
+    assert e.value.status == bqc.BQC_E_INVALID
+    srv.close()
