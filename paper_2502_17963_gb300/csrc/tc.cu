@@ -186,6 +186,7 @@ struct XTile {
   const XpassParams *p;
   int64_t m0;
   int cg, xn;
+  const CUtensorMap *ChH = nullptr, *ClH = nullptr;  // half-height C boxes (cluster pairs)
 };
 
 // Tile locator of a single-problem launch.
@@ -197,12 +198,30 @@ template <int XN> struct XLocOne {
   }
 };
 
+// Tile locator of a cluster pair: pair tile u = (row tiles 2 (u / ncg) and
+// 2 (u / ncg) + 1, column group u % ncg); the CTA of rank r takes row tile
+// 2 (u / ncg) + r.  Both CTAs need the same C tile: each loads one half and
+// multicasts it to both.  A row tile past the end is computed from the
+// (zero-filled or next) rows and discarded by the epilogue's row guard.
+template <int XN> struct XLocPair {
+  const CUtensorMap *Ah, *Al, *Ch, *Cl, *ChH, *ClH;
+  const XpassParams *p;
+  int rank;
+  __device__ __forceinline__ XTile at(int64_t u) const {
+    const int64_t rt = 2 * (u / p->ncg) + rank;
+    return XTile{Ah, Al, Ch, Cl, p, p->row0 + rt * kBM, (int)(u % p->ncg), XN, ChH, ClH};
+  }
+};
+
 // Persistent: CTA c processes tiles c, c + grid, ...; tile t = (row tile
 // t / ncg, column group t % ncg), so neighbouring CTAs share A rows in L2.
+// MC: the CTAs run in clusters of two over pair tiles (XLocPair), the C tile
+// multicast to both, and a stage is free only when both CTAs' MMAs have
+// released it (each MMA warp's commit arrives on both CTAs' empty barrier).
 // EPI 0: X[row][i] (hi/lo) and the fused w_P partials; EPI 1: X^T layout
 // (TF32 only).  KIND: TF32 or FP16 operands (k-blocks of 32 or 64 elements).
 // LOC maps a tile index to its problem (one problem, or a grouped table).
-template <int KIND, int XN, int SPLIT, int EPI, class LOC>
+template <int KIND, int XN, int SPLIT, int EPI, class LOC, bool MC = false>
 __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int stages,
                                            int *flag) {
   static_assert(KIND == kKindTF32 || EPI == 0, "the transposed epilogue is TF32 only");
@@ -230,7 +249,7 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, MC ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -240,14 +259,18 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
   }
   if (warp == 0) tmem_alloc(smem_u32(tslot), TCOLS);
   __syncthreads();
+  if (MC) cluster_sync();  // the peer's barriers exist before anything is multicast
   tc_fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t sbase = smem_u32(smem);
+  const int64_t tbeg = MC ? blockIdx.x / 2 : blockIdx.x;
+  const int64_t tstep = MC ? gridDim.x / 2 : gridDim.x;
+  const uint32_t rank = MC ? cluster_rank() : 0;
   bool ok = true;
   if (warp == 0) {
     if (lane == 0) {
       int64_t kg = 0;  // k-blocks issued by this CTA
-      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (int64_t t = tbeg; t < tiles && ok; t += tstep) {
         const XTile T = loc.at(t);
         const int kblocks = T.p->kblocks;
         const int c0 = T.cg * T.xn;
@@ -262,15 +285,24 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
           mbar_arrive_expect_tx(bar, tx);
           tma_load_2d(a, T.Ah, bar, kb * KE, (int)T.m0);
           if (SPLIT == 3) tma_load_2d(a + a_bytes, T.Al, bar, kb * KE, (int)T.m0);
-          tma_load_2d(a + NS * a_bytes, T.Ch, bar, kb * KE, c0);
-          if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, T.Cl, bar, kb * KE, c0);
+          if (MC) {  // this CTA's half of the C tile, to both CTAs of the pair
+            const int hr = T.xn / 2;
+            const uint32_t ho = rank * (uint32_t)hr * 128;
+            tma_load_2d_mc(a + NS * a_bytes + ho, T.ChH, bar, kb * KE, c0 + (int)rank * hr, 3);
+            if (SPLIT == 3)
+              tma_load_2d_mc(a + NS * a_bytes + c_bytes + ho, T.ClH, bar, kb * KE,
+                             c0 + (int)rank * hr, 3);
+          } else {
+            tma_load_2d(a + NS * a_bytes, T.Ch, bar, kb * KE, c0);
+            if (SPLIT == 3) tma_load_2d(a + NS * a_bytes + c_bytes, T.Cl, bar, kb * KE, c0);
+          }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       int64_t kg = 0, g = 0;
-      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (int64_t t = tbeg; t < tiles && ok; t += tstep) {
         const XTile T = loc.at(t);
         const int kblocks = T.p->kblocks;
         const int ngroups = (kblocks + kGroupKb - 1) / kGroupKb;
@@ -309,7 +341,10 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
                 KD::mma(d, sdesc_sw128(ah + k4 * 32), sdesc_sw128(ch + k4 * 32), acc, idesc);
               }
             }
-            mma_commit(empty0 + 8 * s);
+            if (MC)
+              mma_commit_mc(empty0 + 8 * s, 3);
+            else
+              mma_commit(empty0 + 8 * s);
           }
           mma_commit(tfull0 + 8 * b);
         }
@@ -319,7 +354,7 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
     // epilogue warps: quadrant q of TMEM lanes, column half h
     const int q = warp & 3, h = (warp - 2) >> 2;
     int64_t g = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (int64_t t = tbeg; t < tiles; t += tstep) {
       const XTile T = loc.at(t);
       const XpassParams &p = *T.p;
       const int half = T.xn / 2;  // a multiple of 16
@@ -481,6 +516,9 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
   }
   tc_fence_before();
   __syncthreads();
+  // the peer's MMAs (whose commits arrive here) and its copies into this
+  // CTA's shared memory are complete once both CTAs reach this barrier
+  if (MC) cluster_sync();
   if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
 
@@ -499,6 +537,27 @@ __global__ void __launch_bounds__(kThreads, xpass_min_blocks(XN))
   }
   const XLocOne<XN> loc{&mapAh, &mapAl, &mapCh, &mapCl, &p};
   xpass_body<KIND, XN, SPLIT, EPI>(loc, p.tiles, p.stages, p.flag);
+}
+
+// The split-FP16 X pass in clusters of two CTAs over pair tiles: each CTA
+// loads its own 128 rows of B and one half of the shared C tile, multicast to
+// both, so the C operand crosses from L2 once per pair instead of twice.
+template <int XN>
+__global__ void __launch_bounds__(kThreads, xpass_min_blocks(XN))
+    k_xpass_mc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+               const __grid_constant__ CUtensorMap mapChH,
+               const __grid_constant__ CUtensorMap mapClH, const __grid_constant__ XpassParams p) {
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapAh);
+    prefetch_tmap(&mapAl);
+    prefetch_tmap(&mapChH);
+    prefetch_tmap(&mapClH);
+  }
+  const XLocPair<XN> loc{&mapAh, &mapAl, &mapChH, &mapClH, &mapChH, &mapClH, &p,
+                         (int)cluster_rank()};
+  const int64_t rt = (p.rows + kBM - 1) / kBM;
+  xpass_body<kKindF16, XN, 3, 0, XLocPair<XN>, true>(loc, (rt + 1) / 2 * p.ncg, p.stages,
+                                                     p.flag);
 }
 
 // w[P] = sum over partials and mu of wpart[k][P*N + mu] (FP64); also fp32 w.
@@ -1591,6 +1650,10 @@ struct MixedState {
   MixedPlan plan;
   int shadow = BQC_SHADOW_TF32;
   CUtensorMap mapAh, mapAl, mapCh, mapCl, mapXh, mapXl;
+  // split-FP16 X pass in cluster pairs: C boxes of xn / 2 rows, and the
+  // number of two-CTA clusters that fit at once (0: pairs not used)
+  CUtensorMap mapChH, mapClH;
+  int mc_clusters = 0;
   DBuf Bl, Xl, Cl, Cf, wpart, w32;
   // FP16 split
   DBuf Bh16, Bl16, Xh16, Xl16, Ch16, Cl16, cstat, scale;
@@ -1683,6 +1746,57 @@ static int make_side_stream(Df *df, cudaStream_t s) {
 
 // FP16 split shadows of the stored B: the scale s_B from max|B| and the
 // largest row norm of B (for the per-build bound on |X|), read back once.
+// k_xpass_mc for a runtime tile width; p == nullptr: set its shared-memory
+// attribute and count the two-CTA clusters that fit (into *clusters).
+template <int XN>
+static int xpass_mc_launch(size_t smem, const XpassParams *p, const MixedState *ms, int grid,
+                           cudaStream_t s, int *clusters) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (!p) {
+    BQC_CUDA_TRY(cudaFuncSetAttribute(k_xpass_mc<XN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    cfg.gridDim = dim3(2 * (unsigned)sm_count());
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_xpass_mc<XN>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    *clusters = n;
+    return BQC_OK;
+  }
+  cfg.gridDim = dim3((unsigned)grid);
+  BQC_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_xpass_mc<XN>, ms->mapAh, ms->mapAl, ms->mapChH,
+                                  ms->mapClH, *p));
+  return BQC_OK;
+}
+
+static int xpass_mc_dispatch(int xn, size_t smem, const XpassParams *p, const MixedState *ms,
+                             int grid, cudaStream_t s, int *clusters) {
+#define BQC_XN_MC(V) \
+  case V:            \
+    return xpass_mc_launch<V>(smem, p, ms, grid, s, clusters);
+  switch (xn) { BQC_XN_LIST(BQC_XN_MC) }
+#undef BQC_XN_MC
+  return BQC_E_UNSUPPORTED;
+}
+
+static int xpass_mc_setup(MixedState *ms, int xn, size_t smem) {
+  int n = 0;
+  BQC_TRY(xpass_mc_dispatch(xn, smem, nullptr, ms, 0, nullptr, &n));
+  ms->mc_clusters = n;
+  return BQC_OK;
+}
+
 static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   const Basis *b = df->basis;
   const int n = b->nbf, naux = df->naux_loc;
@@ -1758,7 +1872,11 @@ static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
     const uint32_t box[2] = {64, (uint32_t)m.xn};
     BQC_TRY(make_tmap_f16(&ms->mapCh, ms->Ch16.p, 2, dims, str, box));
     BQC_TRY(make_tmap_f16(&ms->mapCl, ms->Cl16.p, 2, dims, str, box));
+    const uint32_t hbox[2] = {64, (uint32_t)m.xn / 2};
+    BQC_TRY(make_tmap_f16(&ms->mapChH, ms->Ch16.p, 2, dims, str, hbox));
+    BQC_TRY(make_tmap_f16(&ms->mapClH, ms->Cl16.p, 2, dims, str, hbox));
   }
+  BQC_TRY(xpass_mc_setup(ms, m.xn, m.xp_smem[1]));
   {  // X split as (ldx, N, Naux)
     const uint64_t dims[3] = {(uint64_t)m.ldx, (uint64_t)n, (uint64_t)naux};
     const uint64_t str[2] = {(uint64_t)m.ldx * 2, (uint64_t)n * m.ldx * 2};
@@ -1906,8 +2024,14 @@ static int mixed_xpass(Df *df, const double *C, int kind, int split, cudaStream_
   p.q0 = 0;
   p.bkv = 0;
   p.xrows = 0;
-  BQC_TRY(dispatch_xn(m.xn, kind, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl,
-                      grid, s));
+  const int64_t pairs = ((p.rows + kBM - 1) / kBM + 1) / 2 * m.ncg;
+  if (kind == kKindF16 && ms->mc_clusters > 0 && Ah == &ms->mapAh && pairs >= 2) {
+    const int g2 = 2 * (int)std::min<int64_t>(ms->mc_clusters, pairs);
+    BQC_TRY(xpass_mc_dispatch(m.xn, m.xp_smem[k], &p, ms, g2, s, nullptr));
+  } else {
+    BQC_TRY(dispatch_xn(m.xn, kind, split, 0, m.xp_smem[k], &p, Ah, Al, &ms->mapCh, &ms->mapCl,
+                        grid, s));
+  }
   if (w_out) {
     k_wreduce<<<(unsigned)(P1 - P0), 256, 0, s>>>(ms->wpart.as<float>(), rows, 2 * m.ncg, n,
                                                    w_out, ms->w32.as<float>(),
