@@ -298,6 +298,11 @@ __device__ __forceinline__ void xpass_body(const LOC &loc, int64_t tiles, int st
           }
         }
       }
+      // MC tail: wait until both CTAs' MMAs have released the last stages,
+      // so that no commit of the peer can still be on its way to this CTA's
+      // barriers when the CTA exits
+      for (int64_t j = kg > stages ? kg - stages : 0; MC && ok && j < kg; ++j)
+        ok = mbar_wait(empty0 + 8 * (int)(j % stages), (uint32_t)((j / stages) & 1), flag, 15);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -1744,8 +1749,6 @@ static int make_side_stream(Df *df, cudaStream_t s) {
   return BQC_OK;
 }
 
-// FP16 split shadows of the stored B: the scale s_B from max|B| and the
-// largest row norm of B (for the per-build bound on |X|), read back once.
 // k_xpass_mc for a runtime tile width; p == nullptr: set its shared-memory
 // attribute and count the two-CTA clusters that fit (into *clusters).
 template <int XN>
@@ -1797,6 +1800,8 @@ static int xpass_mc_setup(MixedState *ms, int xn, size_t smem) {
   return BQC_OK;
 }
 
+// FP16 split shadows of the stored B: the scale s_B from max|B| and the
+// largest row norm of B (for the per-build bound on |X|), read back once.
 static int mixed_setup_f16(Df *df, MixedState *ms, cudaStream_t s) {
   const Basis *b = df->basis;
   const int n = b->nbf, naux = df->naux_loc;

@@ -47,7 +47,7 @@ def test_grouped_equals_single(gpu_ctx, bqc, names):
     Js, Ks = bqc.jk_grouped(dfs, Cs)
     torch.cuda.synchronize()
     for (J1, K1), J2, K2, nm in zip(ref, Js, Ks, names):
-        assert torch.equal(K1, K2), nm
+        assert torch.equal(K1, K2), (nm, float((K1 - K2).abs().max()), float(K1.abs().max()))
         # J: float-float sums (~2^-46 per term) over a different aux
         # chunking; J cancels by up to ~100x against its terms here
         ja = float(J1.abs().max())
