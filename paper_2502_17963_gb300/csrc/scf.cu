@@ -529,14 +529,16 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     }
     const bool e_stable =
         have_prev && std::fabs(E - Eprev) < std::max(o.energy_tol, DBL_EPSILON * n * std::fabs(E));
-    if (stage == BQC_PREC_FP64 && emax < o.diis_tol && (e_stable || confirming)) {
+    if (stage == BQC_PREC_FP64 && emax < o.diis_tol &&
+        (e_stable || confirming || last_incremental)) {
       if (!last_incremental) {
         converged = true;
         break;
       }
-      // converged on an incremental Fock matrix (energy stable within the
-      // increments of one anchor, which share their rounding): redo the
-      // iteration as a full FP64 build, which must confirm the DIIS error
+      // converged on an incremental Fock matrix: redo the iteration as a full
+      // FP64 build, which must confirm the DIIS error (an incremental energy
+      // carries the increment's rounding, so its stability is not required
+      // here; the confirming build's own DIIS error decides)
       need_anchor = true;
       confirming = true;
       --it;
