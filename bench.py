@@ -806,7 +806,7 @@ def main():
     if args.prec == "f16x3":
         esz = 2
         peak = sust  # dense fp16 and bf16 run at the same tensor rate
-        kern = "k_xpass<f16,XN,3,0> (X = B C, split FP16, 3 products)"
+        kern = "k_xpass_mc<XN> (X = B C, split FP16, 3 products, two-CTA clusters)"
         peak_src = f"{pk_src}: bf16 sustained (the fp16 dense rate equals bf16's)"
         traffic = None  # no ncu capture of this kernel's DRAM bytes yet
         traffic_src = "not captured for the FP16 kernel"
@@ -837,9 +837,10 @@ def main():
         "phases_ms": {"x_pass": ph_mean[0], "j_pass": ph_mean[1], "k_syrk": ph_mean[2],
                       "prep": ph_mean[3]},
         "j_pass_gbs_beside_syrk": jbytes / (ph_mean[1] * 1e-3) / 1e9,
-        "j_note": "J pass (FP64 FMAs over the packed FP64 B, w fused in the X pass) on a side "
-                  "stream concurrent with the SYRK, timed from the fork to its end, so the "
-                  "rate includes the contention (alone: 10.5 ms, 4.7 TB/s, FP64-pipe bound)",
+        "j_note": ("J pass (split-FP16 build: float-float FMAs on the FP32 pipe over the "
+                   "float-pair copy of B, in four aux pieces on a side stream beside the X-pass "
+                   "pieces and the SYRK), timed from the end of the first X piece to its end, so "
+                   "the rate includes the contention; alone see coulomb"),
         "k_syrk_tflops": kflops / (ph_mean[2] * 1e-3) / 1e12,
         "k_syrk_frac": kflops / (ph_mean[2] * 1e-3) / 1e12 / tf32_peak,
         "tensor_peak_tflops": tf32_peak,
