@@ -282,10 +282,11 @@ int bqc_df_coulomb(bqc_df *df, const double *D_dev, double *J_dev, int variant,
  * device, and appear once.  The X passes of all molecules run as one
  * persistent tensor-core launch, then their FP64 J passes as one launch and
  * their SYRKs as one launch (up to 12 molecules per launch; more are taken
- * twelve at a time), each molecule keeping its own plan, so J[k] and K[k]
- * equal bqc_jk's K exactly and its J to the rounding of the J pass's aux
- * chunking.  Uses each handle's own workspace: no handle may have another
- * build in flight.  Async on `stream`. */
+ * twelve at a time), each molecule keeping its own plan, so K[k] equals
+ * bqc_jk's K exactly and J[k] its J to the float-float rounding of a
+ * different aux chunking (~1e-12 of max|J|).  Uses each handle's own
+ * workspace: no handle may have another build in flight.  Async on
+ * `stream`. */
 int bqc_jk_grouped(int n, bqc_df *const *dfs, const double *const *C_dev, double *const *J,
                    double *const *K, bqc_stream_t stream);
 
