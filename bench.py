@@ -235,7 +235,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(mol, "oracle"),
+            "data": "synthetic", "config": config(mol, "mixed_" + args.prec),
+            "reference_is": "the FP64 CPU oracle (oracle.jk_df), timed on the host cores",
             "step_is": f"a {nsample}/{naux} sample of one Fock build",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -251,7 +252,7 @@ def config(mol, prec):
                         f"nocc={mol.nocc}", "prec": prec, "seed": len(mol.Z) // 3,
             "l2": f"inputs larger than L2 (per step: {naux * n * n * 2 * esz / 1e9:.1f} GB "
                   f"of split B shadows read by the X pass, {naux * n * (n + 1) / 2 * 8 / 1e9:.1f} GB "
-                  "of FP64 B by the J pass)",
+                  + ("of float-pair B by the J pass)" if esz == 2 else "of FP64 B by the J pass)"),
             "parallelism": "replicas"}
 
 
