@@ -35,6 +35,10 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes / algorithmic bytes of k_xpass_tf32<.,3> in an ncu capture at
 # (H2O)_16 (1.905 GB / 1.843 GB); both grow as Naux x N x (N + nocc)
 XPASS_TRAFFIC_RATIO = 1.034
+# the same ratio for the split-FP16 X pass in two-CTA clusters (k_xpass_mc,
+# full capture of one aux piece at (H2O)_20: 457.0 MB of DRAM traffic against
+# 474.0 MB of algorithmic bytes); the operand layout sets it per unit of work
+XPASS_F16_TRAFFIC_RATIO = 0.964
 
 
 def parse():
@@ -809,8 +813,11 @@ def main():
         peak = sust  # dense fp16 and bf16 run at the same tensor rate
         kern = "k_xpass_mc<XN> (X = B C, split FP16, 3 products, two-CTA clusters)"
         peak_src = f"{pk_src}: bf16 sustained (the fp16 dense rate equals bf16's)"
-        traffic = None  # no ncu capture of this kernel's DRAM bytes yet
-        traffic_src = "not captured for the FP16 kernel"
+        xb16 = naux * n * n * 2 * esz + naux * n * no * 2 * esz
+        traffic = XPASS_F16_TRAFFIC_RATIO * xb16
+        traffic_src = ("ncu dram__bytes_read+write / algorithmic bytes of k_xpass_mc at (H2O)_20 "
+                       f"({XPASS_F16_TRAFFIC_RATIO}, one aux piece) x this X pass's bytes "
+                       f"({xb16:.4g} B, all four pieces)")
     else:
         esz = 4
         peak = sust * TF32_OVER_BF16
