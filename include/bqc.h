@@ -339,6 +339,12 @@ typedef struct {
   int incremental;     /* staged SCF only (prec mixed): 0 = every FP64-stage Fock
                           build is a full FP64 build; 1 = anchored incremental
                           FP64 stage (see bqc_scf_run)                         */
+  const double *guess_C; /* optional start (resume from a checkpoint): device
+                          N x nocc row-major occupied orbitals, e.g. the first
+                          nocc columns of an earlier result's C_dev; the first
+                          Fock build uses D = C C^T instead of the
+                          core-Hamiltonian guess, and the DIIS history starts
+                          empty.  NULL: core guess.  Ignored by the server.   */
 } bqc_scf_opts;
 
 typedef struct {

@@ -60,7 +60,8 @@ class bqc_scf_opts(ctypes.Structure):
     _fields_ = [("diis_tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
                 ("stage_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_space", ctypes.c_int), ("prec", ctypes.c_int),
-                ("orth_thresh", ctypes.c_double), ("incremental", ctypes.c_int)]
+                ("orth_thresh", ctypes.c_double), ("incremental", ctypes.c_int),
+                ("guess_C", ctypes.c_void_p)]
 
 
 class bqc_scf_result(ctypes.Structure):
@@ -441,15 +442,17 @@ def mp2(df: DF, C, eps, prec: int = PREC_FP64, stream=None) -> float:
 def scf_run(ctx: Context, df: DF, prec: int = PREC_FP64, diis_tol: float = 1e-8,
             energy_tol: float = 1e-10, stage_tol: float = 1e-5, max_iter: int = 100,
             diis_space: int = 8, orth_thresh: float = 1e-8, stream=None, keep_arrays=False,
-            incremental: bool = False):
+            incremental: bool = False, guess=None):
     """Runs bqc_scf_run; returns a dict (energy, iterations, converged, ...,
     history = [(prec, DIIS error, energy)] per Fock build).
 
     With keep_arrays the MO coefficients (N x nmo), orbital energies and the
-    last Fock matrix come back as device tensors.
+    last Fock matrix come back as device tensors.  guess: a contiguous
+    N x nocc device tensor of occupied orbitals to start from (resume from a
+    checkpoint, e.g. result["C"][:, :nocc].contiguous()).
     """
     o = bqc_scf_opts(diis_tol, energy_tol, stage_tol, max_iter, diis_space, prec, orth_thresh,
-                     1 if incremental else 0)
+                     1 if incremental else 0, _ptr(guess) if guess is not None else None)
     r = bqc_scf_result()
     n = df.basis.nbf
     cap = 2 * max_iter + 2

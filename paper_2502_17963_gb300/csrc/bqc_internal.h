@@ -15,6 +15,15 @@
 
 namespace bqc {
 
+// NVTX range over a host scope (a profiler attached by nsys or ncu's NVTX
+// filter shows it; without one it costs two calls into a stub).
+struct NvtxRange {
+  explicit NvtxRange(const char *name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Cancellation flag of the request the calling thread is solving (serving),
 // read by the SCF between iterations; null outside the server.
 extern thread_local const std::atomic<int> *tl_cancel;

@@ -562,6 +562,7 @@ int bqc_df_build(bqc_ctx *ctx, const bqc_basis *basis, const bqc_df_opts *opts,
                  bqc_stream_t stream, bqc_df **out) {
   if (!ctx || !basis || !out) return BQC_E_INVALID;
   *out = nullptr;
+  NvtxRange nv("bqc_df_build");
   BQC_CUDA_TRY(cudaSetDevice(ctx->device));
   bqc_df_opts o;
   o.mode = BQC_DF_STORED;
@@ -776,6 +777,7 @@ int bqc_jk(bqc_df *df, const double *C, int nocc, int prec, double *J, double *K
            bqc_stream_t stream) {
   if (!df || !C || !J || !K) return BQC_E_INVALID;
   if (nocc != df->basis->nocc) return BQC_E_INVALID;
+  NvtxRange nv(prec == BQC_PREC_FP64 ? "bqc_jk fp64" : "bqc_jk mixed");
   cudaStream_t s = (cudaStream_t)stream;
   if (df->timing) df->timed = true;
   df->last_mixed = prec != BQC_PREC_FP64;

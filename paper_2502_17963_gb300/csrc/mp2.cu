@@ -179,6 +179,7 @@ using namespace bqc;
 extern "C" int bqc_mp2(bqc_df *df, const double *C_dev, const double *eps_dev, int nmo, int prec,
                        double *e2, bqc_stream_t stream) {
   if (!df || !C_dev || !eps_dev || !e2) return BQC_E_INVALID;
+  NvtxRange nv("bqc_mp2");
   if (df->mode != BQC_DF_STORED || !df->B64.p || !df->X64.p || df->is_shard()) {
     set_error("bqc_mp2 needs a stored-mode DF handle holding the whole tensor", __FILE__, __LINE__);
     return BQC_E_INVALID;

@@ -3,6 +3,7 @@
 // on the device (Sec. 2.2.2 item 3): the host only normalises the shells and
 // lays out index lists; every integral is evaluated by the kernels in eri.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -15,6 +16,9 @@
 namespace bqc {
 
 thread_local const std::atomic<int> *tl_cancel = nullptr;
+
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 static thread_local char g_err[512] = "";
 

@@ -66,6 +66,14 @@ __global__ void k_orth(int n, int nmo, int k0, const double *U, const double *s,
 }
 
 // row-major out[r][c] = colmajor in[c * rows + r]  (rows x cols)
+// out (column-major, leading dimension ld) = in (row-major rows x cols)
+__global__ void k_rm_to_cm(int rows, int cols, const double *in, double *out, int64_t ld) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows * cols) return;
+  const int64_t r = i / cols, c = i % cols;
+  out[c * ld + r] = in[i];
+}
+
 __global__ void k_cm_to_rm(int rows, int cols, const double *in, int64_t ld, double *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)rows * cols) return;
@@ -260,6 +268,10 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
     return BQC_OK;
   };
   BQC_TRY(diag(H.as<double>()));
+  if (o.guess_C) {  // resume: the given occupied orbitals replace the core guess's
+    k_rm_to_cm<<<nblk((int64_t)n * no), 256, 0, s>>>(n, no, o.guess_C, Cc.as<double>(), n);
+    BQC_LAUNCH_CHECK();
+  }
   const int space = std::max(1, o.diis_space);
   std::vector<DBuf> hF(space), hE(space);
   for (int i = 0; i < space; ++i) {
@@ -432,6 +444,9 @@ int scf_run(Ctx *ctx, Df *df, const bqc_scf_opts &o, cudaStream_t s, bqc_scf_res
   const bool use_graph = df->mode == BQC_DF_STORED && !df->timing && s != nullptr;
   auto graph_free = [&]() { graphs.clear(); };
   for (it = 1; it <= o.max_iter; ++it) {
+    NvtxRange nv(stage != BQC_PREC_FP64 ? "scf iteration, mixed"
+                 : inc_on && !need_anchor ? "scf iteration, incremental"
+                                          : "scf iteration, fp64");
     if (cancel_requested()) {  // between iterations: nothing of ours in flight
       BQC_CUDA_TRY(cudaStreamSynchronize(s));
       return BQC_E_CANCELLED;

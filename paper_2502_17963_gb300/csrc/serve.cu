@@ -187,6 +187,7 @@ size_t serve_footprint(int n, int naux, int nocc, int shadow) {
 }
 
 static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
+  NvtxRange nv("serve request");
   std::vector<bqc_shell> sh[2];
   for (int k = 0; k < 2; ++k) {
     size_t po = 0;
@@ -217,6 +218,7 @@ static void run_request(bqc_server *srv, Request *r, cudaStream_t s) {
   if (st == BQC_OK && srv->group) df->group = srv->group;
   if (st == BQC_OK) {
     bqc_scf_opts so = srv->opts.scf;
+    so.guess_C = nullptr;  // every request starts from its own core guess
     so.prec = srv->opts.prec;
     st = bqc_scf_run(srv->ctx, df, &so, (bqc_stream_t)s, &res);
   }

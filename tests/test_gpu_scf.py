@@ -47,3 +47,23 @@ def test_scf_on_own_stream_graph_replay(gpu_ctx, bqc, prec):
     assert r["converged"] and r0["converged"]
     assert abs(r["energy"] - r0["energy"]) < 1e-10
     assert r["iterations"] == r0["iterations"]
+
+
+def test_scf_resume_from_checkpoint(gpu_ctx, bqc):
+    """Checkpoint / resume: an SCF stopped after a few iterations restarts
+    from its occupied orbitals (bqc_scf_opts.guess_C) and reaches the
+    uninterrupted energy; restarting from converged orbitals converges at
+    once."""
+    mol = workload.molecule_for("w4")
+    basis = bqc.Basis(gpu_ctx, mol)
+    df = bqc.DF(gpu_ctx, basis)
+    no = basis.nocc
+    full = bqc.scf_run(gpu_ctx, df, prec=bqc.PREC_FP64)
+    part = bqc.scf_run(gpu_ctx, df, prec=bqc.PREC_FP64, max_iter=4, keep_arrays=True)
+    assert full["converged"] and not part["converged"]
+    res = bqc.scf_run(gpu_ctx, df, prec=bqc.PREC_FP64, keep_arrays=True,
+                      guess=part["C"][:, :no].contiguous())
+    assert res["converged"] and abs(res["energy"] - full["energy"]) < 1e-8
+    again = bqc.scf_run(gpu_ctx, df, prec=bqc.PREC_FP64, guess=res["C"][:, :no].contiguous())
+    assert again["converged"] and again["iterations"] <= 3, again
+    assert abs(again["energy"] - full["energy"]) < 1e-8
