@@ -435,7 +435,8 @@ typedef enum {
 typedef struct {
   int max_slots;       /* concurrent SCF solves on the device (default 4)     */
   size_t hbm_budget;   /* bytes the admitted requests may hold (0 = ctx's)    */
-  int prec;            /* bqc_prec of every request                           */
+  int prec;            /* bqc_prec of every request (MIXED_F16X3 when the
+                          server is created with opts NULL)                    */
   bqc_scf_opts scf;    /* SCF options for every request                       */
   int policy;          /* bqc_serve_policy                                    */
   int max_skips;       /* backfill starvation bound (<= 0: 8)                 */

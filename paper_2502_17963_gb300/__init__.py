@@ -481,7 +481,7 @@ class Server:
     """bqc_server: continuous batching of SCF solves (see bqc_serve_create)."""
 
     def __init__(self, ctx: Context, max_slots: int = 4, hbm_budget: int = 0,
-                 prec: int = PREC_MIXED_TF32X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
+                 prec: int = PREC_MIXED_F16X3, diis_tol: float = 1e-8, energy_tol: float = 1e-10,
                  stage_tol: float = 1e-5, max_iter: int = 100, diis_space: int = 8,
                  orth_thresh: float = 1e-8, policy: int = 0, max_skips: int = 8,
                  incremental: bool = False, grouped: bool = False,
@@ -557,5 +557,5 @@ def jk_grouped(dfs, Cs, Js=None, Ks=None, stream=None):
     return Js, Ks
 
 
-def serve_footprint(nbf: int, naux: int, nocc: int, prec: int = PREC_MIXED_TF32X3) -> int:
+def serve_footprint(nbf: int, naux: int, nocc: int, prec: int = PREC_MIXED_F16X3) -> int:
     return int(lib().bqc_serve_footprint(nbf, naux, nocc, prec))

@@ -349,7 +349,7 @@ int bqc_serve_create(bqc_ctx *ctx, const bqc_serve_opts *opts, bqc_server **out)
   bqc_serve_opts o{};
   o.max_slots = 4;
   o.hbm_budget = 0;
-  o.prec = BQC_PREC_MIXED_TF32X3;
+  o.prec = BQC_PREC_MIXED_F16X3;
   o.scf.diis_tol = 1e-8;
   o.scf.energy_tol = 1e-10;
   o.scf.stage_tol = 1e-5;

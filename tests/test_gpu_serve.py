@@ -116,8 +116,8 @@ def test_alone_equals_mix_sampled_stream(gpu_ctx, bqc, prec, tol):
 @pytest.mark.parametrize("policy", [0, 1])
 def test_backfill_admission_and_priority(gpu_ctx, bqc, policy):
     big, small = workload.water_cluster(6), workload.single_water()
-    fb = bqc.serve_footprint(150, 450, 30)
-    fs = bqc.serve_footprint(26, 92, 5)
+    fb = bqc.serve_footprint(150, 450, 30, prec=2)
+    fs = bqc.serve_footprint(26, 92, 5, prec=2)
     assert fs < fb
     # two large requests never fit together, a large and a small one do
     srv = bqc.Server(gpu_ctx, max_slots=3, prec=2, hbm_budget=2 * fb - 1, policy=policy)
