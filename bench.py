@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-policy", choices=["backfill", "fifo"], default="backfill")
-    ap.add_argument("--serve-precs", default="mixed_tf32x3,fp64")
+    ap.add_argument("--serve-precs", default="mixed_f16x3,fp64")
     ap.add_argument("--scf", action="store_true",
                     help="time one precision-staged SCF (--prec, then FP64) at --waters")
     ap.add_argument("--incremental", action="store_true",
